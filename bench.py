@@ -1,0 +1,377 @@
+"""Benchmark of EP-HDC client-side encrypted inference on one GB300 per rank.
+
+A step is one pass of the whole client path over one batch of synthetic queries:
+HDC projection + quantisation, BFV batch encoding (slot packing, inverse NTT mod
+t, lift, NTT per limb), plaintext x ciphertext multiply-accumulate against the
+device-resident encrypted model, rotate-and-sum with key switching, and the
+inverse NTT of the score ciphertexts.  The encrypted model and the rotation keys
+are made once before timing (server side, not part of the client path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload face1024]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+Under torchrun every rank runs an independent replica (the path has no exchange
+step), so the value is the queries of all ranks over the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted HDC queries/sec (D=10000, n=8192) and % HBM/INT8 roofline vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="face1024")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-perquery", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_units(w, B, units, seed):
+    """Time the oracle's client path on `units` plaintext indices (D-chunks) of one
+    batch of B queries, and separately its per-batch tail (rotate-and-sum).  Returns
+    (seconds for the units, seconds for the tail, threads)."""
+    import oracle as O
+    from paper_2511_00737_gb300 import workload as WL
+    Dsub = min(w.D, units * w.r)
+    osub = O.Oracle(w.n, w.L, w.k, w.k_in, w.r, Dsub)
+    X = WL.features(seed, B, w.F)
+    Wt = WL.projection(seed, w.D, w.F)[:Dsub]
+    cls = WL.classes(seed, w.k, w.D)[:, :Dsub]
+    s, gk = osub.keygen(seed)
+    model = osub.encrypt_model(seed, np.ascontiguousarray(cls), s)  # setup, not timed
+    t0 = time.perf_counter()
+    H = O.hdc_encode(X, np.ascontiguousarray(Wt), w.shift, w.bits)
+    m = osub.encode_plain(H)
+    acc = osub.ptct_mac(m, B, model)
+    t1 = time.perf_counter()
+    osub.rotate_sum(gk, acc)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, O.num_threads()
+
+
+def cpu_baseline(w, B, budget_s, seed):
+    import oracle as O
+    P = -(-w.D // w.r)
+    # calibrate on one unit, then size the sample to the budget
+    t_one, t_tail, cores = oracle_units(w, B, 1, seed)
+    units = int(max(1, min(P, budget_s / max(t_one, 1e-3))))
+    t_units, t_tail, cores = oracle_units(w, B, units, seed)
+    est = t_units * P / units + t_tail
+    return {"value": B / est, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of %d plaintext indices of one %d-query batch (%.1f s) plus the "
+                      "rotate-and-sum tail (%.2f s), scaled to the full batch" % (
+                          units, P, B, t_units, t_tail)}
+
+
+def run_reference(args, w, B):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    P = -(-w.D // w.r)
+    budget = max(0.02, 150.0 / max(1, args.steps + args.warmup))
+    t_one, t_tail, cores = oracle_units(w, B, 1, w.seed)
+    units = int(max(1, min(P, budget / max(t_one, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_units(w, B, units, w.seed)
+    tot = 0.0
+    for _ in range(args.steps):
+        t, _, cores = oracle_units(w, B, units, w.seed)
+        tot += t
+    per_unit = tot / (args.steps * units)
+    est = per_unit * P + t_tail
+    value = B / est
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est * 1000.0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "impl": "reference",
+            "config": config_of(w, B),
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "%d of %d plaintext indices per step, %d steps, plus the "
+                                       "rotate-and-sum tail" % (units, P, args.steps)},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, B):
+    return {"workload": "%s: B=%d queries, F=%d, D=%d, %d-bit HVs, k=%d classes, BFV n=%d, "
+                        "t=65537, L=%d x 30-bit primes, layout k_in=%d r=%d" % (
+                            w.name, B, w.F, w.D, w.bits, w.k, w.n, w.L, w.k_in, w.r),
+            "global_batch": B, "n": w.n, "L": w.L, "D": w.D, "F": w.F, "k": w.k,
+            "hv_bits": w.bits, "k_in": w.k_in, "r": w.r,
+            "l2": "inputs larger than L2: the encrypted model streamed every step is "
+                  "larger than the 129 MB L2", "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, w, B):
+    import torch
+    from paper_2511_00737_gb300 import ephdc as E
+    from paper_2511_00737_gb300 import workload as WL
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    ctx = E.Context.for_workload(w, max_batch=B)
+    seed = w.seed + 7919 * rank
+    sk, gk = ctx.keygen(seed)
+    cls = torch.from_numpy(WL.classes(seed, w.k, w.D)).to(dev)
+    model = ctx.encrypt_model(cls, sk, seed)
+    Wt = torch.from_numpy(WL.projection(seed, w.D, w.F)).to(dev)
+    R = 4
+    Xh = [torch.from_numpy(WL.features(seed, B, w.F, batch=b)).pin_memory() for b in range(R)]
+    Xd = [x.to(dev) for x in Xh]
+    out = ctx.out_ct(B)
+    out_h = torch.empty(out.shape, dtype=out.dtype).pin_memory()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def maxall(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    st = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        ctx.infer(Xd[i % R], Wt, model, gk, out=out)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for i in range(args.steps):
+        ctx.infer(Xd[i % R], Wt, model, gk, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    stage_ms, stage_calls, launches = ctx.profile_read()
+    ctx.profile(False)
+    ms = maxall(e0.elapsed_time(e1)) / args.steps
+    value = world * B / (ms / 1000.0)
+
+    # end to end: pinned host inputs in, score ciphertexts back to pinned host
+    ksteps = max(1, min(args.steps, 300))
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in range(ksteps):
+        xd = Xd[i % R]
+        xd.copy_(Xh[i % R], non_blocking=True)
+        ctx.infer(xd, Wt, model, gk, out=out)
+        out_h.copy_(out, non_blocking=True)
+    e1.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = maxall(e0.elapsed_time(e1)) / ksteps
+    e2e = {"value": world * B / (ms_e2e / 1000.0), "unit": "queries/s",
+           "h2d_bytes_per_step": int(B * w.F), "d2h_bytes_per_step": int(out.numel() * 4),
+           "ms_per_step": ms_e2e}
+
+    # the per-query GPU form: one query per call, packed so that log2(n/(2 k_in))
+    # rotations fold the whole hypervector (the dense shape of HE-HDC)
+    perq = None
+    if not args.no_perquery and rank == 0:
+        perq = per_query_form(w, dev)
+
+    # roofline of the dominant stage
+    pk, src = peaks()
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    roof = roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, B, args.cpu_budget_s, seed)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic", "config": config_of(w, B),
+                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "cpu_baseline": cpu,
+                "stages_ms_per_step": {k: v / max(1, args.steps) for k, v in stage_ms.items()},
+                "per_query_form": perq}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def per_query_form(w, dev, queries=32):
+    import torch
+    from paper_2511_00737_gb300 import ephdc as E
+    from paper_2511_00737_gb300 import workload as WL
+    kin = w.k
+    r = w.n // (2 * kin)
+    r = 1 << int(math.log2(r))
+    ctx = E.Context(w.n, w.L, w.k, kin, r, w.D, w.F, w.bits, w.shift, 1)
+    sk, gk = ctx.keygen(w.seed)
+    model = ctx.encrypt_model(torch.from_numpy(WL.classes(w.seed, w.k, w.D)).to(dev), sk, w.seed)
+    Wt = torch.from_numpy(WL.projection(w.seed, w.D, w.F)).to(dev)
+    X = torch.from_numpy(WL.features(w.seed, queries, w.F)).to(dev)
+    out = ctx.out_ct(1)
+    for i in range(3):
+        ctx.infer(X[i:i + 1], Wt, model, gk, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(queries):
+        ctx.infer(X[i:i + 1].contiguous(), Wt, model, gk, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / queries
+    ctx.close()
+    return {"value": 1000.0 / ms, "unit": "queries/s", "ms_per_query": ms,
+            "layout": "k_in=%d r=%d (%d rotations per query)" % (kin, r, int(math.log2(r)))}
+
+
+def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
+    G = ctx.groups(B)
+    P, Kp, L, n = ctx.P, ctx.Kp, ctx.L, ctx.n
+    calls = max(1, stage_calls[dom])
+    t = stage_ms[dom] / calls / 1000.0
+    if dom == "mac":
+        model = P * Kp * 2 * L * n * 4
+        pt = G * P * L * n * 4
+        acc = G * Kp * 2 * L * n * 4
+        byts = model + pt + acc
+        ach = byts / t / 1e9
+        return {"kernel": "ptct_mac (+split reduce)", "bound": "hbm", "achieved": ach,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": None, "algorithmic_bytes": byts, "peak_source": src,
+                "ms_per_launch": t * 1000.0}
+    if dom == "encode_plain":
+        # integer-pipe bound: butterflies per second against the issue limit
+        bfly = G * P * (L + 1) * (n // 2) * int(math.log2(n))
+        ach = bfly / t / 1e12
+        return {"kernel": "encode_plain", "bound": "alu", "achieved": ach,
+                "peak": alu_peak_tbfly(pk), "unit": "Tbutterfly/s",
+                "frac": ach / alu_peak_tbfly(pk), "traffic": None, "peak_source": "derived",
+                "ms_per_launch": t * 1000.0}
+    if dom == "hdc_encode":
+        ops = 2.0 * B * w.F * w.D
+        ach = ops / t / 1e12
+        return {"kernel": "hdc_encode", "bound": "tensor", "achieved": ach,
+                "peak": pk["bf16_tflops"] * 2, "unit": "TOP/s", "frac": ach / (pk["bf16_tflops"] * 2),
+                "traffic": None, "peak_source": src + " (bf16 x 2 nominal int8 ratio)",
+                "ms_per_launch": t * 1000.0}
+    return {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None,
+            "frac": None, "traffic": None, "ms_per_launch": t * 1000.0}
+
+
+def alu_peak_tbfly(pk):
+    # 152 SMs x 4 SM sub-partitions x 32 lanes x clock, one 32-bit instruction per lane
+    # per cycle; a lazy Shoup butterfly issues 8 integer instructions (3 multiplies,
+    # 5 adds/selects), so the issue-limited rate is lanes x clock / 8
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return 152 * 4 * 32 * mhz * 1e6 / 8 / 1e12
+
+
+def main():
+    args = parse()
+    from paper_2511_00737_gb300 import workload as WL
+    w = WL.config(args.workload)
+    B = w.B
+    if args.impl == "reference":
+        run_reference(args, w, B)
+    else:
+        run_ours(args, w, B)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * ephdc.h -- C ABI of the GB300 (sm_103a) EP-HDC client-side inference library.
+ *
+ * EP-HDC ("Hyperdimensional Computing with Encrypted Parameters") runs HDC
+ * inference on the client against a BFV-encrypted model (Sec. 4.1): the client
+ * encodes its samples into quantised hypervectors in plaintext (Sec. 2.1,
+ * Sec. 5.1), batch-encodes element d of many query hypervectors into the SIMD
+ * slots of one plaintext (Sec. 3, the SIMD representation), multiplies the
+ * plaintexts with the encrypted class hypervectors and accumulates (Sec. 4.1,
+ * "HE compute"), and returns one ciphertext of similarity scores per batch.
+ * Galois rotation with key switching (Sec. 2.2) folds D-chunks that share a
+ * plaintext into the per-class score.
+ *
+ * Conventions for every entry point:
+ *  - All pointers named *_dev are device pointers owned by the caller; sizes come
+ *    from the ephdc_*_bytes queries.  Device pointers must be 16-byte aligned.
+ *    The library owns only its context (tables, scratch workspace).
+ *  - Work is enqueued asynchronously on the given CUDA stream (NULL = legacy
+ *    default stream).  Argument errors are detected on the host before anything is
+ *    enqueued and return EPHDC_EINVAL (or EPHDC_EUNSUPPORTED) with a message in
+ *    ephdc_last_error(); launch failures return EPHDC_ECUDA.
+ *  - A context is not thread-safe: use one context per host thread (or serialise).
+ *  - No exception crosses the ABI.  No call falls back to the CPU.
+ *  - Ciphertexts exchanged with the host ("coefficient domain") are u32 words in
+ *    [0, q_l), layout [2 polys][L limbs][n coefficients]; the number-theoretic-
+ *    transform (NTT) domain storage order of device buffers is private.
+ *
+ * Parameters: ring degree n (power of two, 1024..16384), L RNS primes q_l < 2^30
+ * with q_l = 1 (mod 2n) (the L largest such primes), plaintext modulus t = 65537,
+ * ternary secret, discrete Gaussian error (sigma, support [-19, 19]).
+ * Slot layout (k_in, r): each plaintext carries r consecutive elements of every
+ * query hypervector (D-chunks); a chunk spans W = n/(2r) slots of each of the two
+ * slot rows and holds k_in classes side by side, cap_row = floor(W / k_in) queries
+ * each; a group of cap = 2*cap_row queries needs P = ceil(D/r) plaintexts.
+ * r = 1 with k_in = k is the paper's representation (batch floor(N/k), D MulCP,
+ * no rotation); r > 1 adds log2(r) rotations per output ciphertext.
+ */
+#ifndef EPHDC_H
+#define EPHDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EPHDC_OK = 0,
+  EPHDC_EINVAL = -1,       /* bad argument (size, pointer, alignment, parameter)   */
+  EPHDC_EUNSUPPORTED = -2, /* valid but not supported by this build               */
+  EPHDC_ENOMEM = -3,       /* device allocation failed / batch above the reserve  */
+  EPHDC_ECUDA = -4,        /* a CUDA call or kernel launch failed                 */
+  EPHDC_ETIMEOUT = -5,     /* a bounded device wait gave up                       */
+  EPHDC_EBUSY = -6         /* resource in use                                      */
+} ephdc_status;
+
+typedef struct {
+  uint32_t n;         /* ring degree, power of two in [1024, 16384]               */
+  uint32_t L;         /* number of RNS primes, 2..8                               */
+  uint32_t k;         /* number of classes                                        */
+  uint32_t k_in;      /* classes packed per ciphertext (divides k)                */
+  uint32_t r;         /* D-chunks folded per plaintext (power of two)            */
+  uint32_t D;         /* hypervector dimension                                     */
+  uint32_t F;         /* feature count (multiple of 16)                           */
+  uint32_t hv_bits;   /* query hypervector precision b, 2..8                      */
+  int32_t shift;      /* quantiser shift s >= 0                                   */
+  uint32_t max_batch; /* largest batch B any call on this context will use        */
+  double sigma;       /* error standard deviation (3.2)                           */
+} ephdc_params;
+
+typedef struct ephdc_ctx ephdc_ctx; /* opaque, owned by the library */
+
+/* Create a context: validates params, derives primes, roots, twiddle and slot
+ * tables, and reserves scratch for batches up to params->max_batch.  Returns
+ * EPHDC_EINVAL for invalid parameters, EPHDC_ENOMEM if device memory runs out,
+ * EPHDC_ECUDA if no device is usable.  *out is NULL on failure. */
+ephdc_status ephdc_ctx_create(const ephdc_params* params, ephdc_ctx** out);
+void ephdc_ctx_destroy(ephdc_ctx* ctx);
+/* Message of the last failing call on this context ("" if none); valid until the
+ * next call on the context.  ctx may be NULL (message of the last failed create). */
+const char* ephdc_last_error(const ephdc_ctx* ctx);
+
+/* Derived quantities: which = "cap" (queries per group), "P" (plaintexts per
+ * group), "Kp" (ciphertexts per plaintext index = k/k_in), "W", "cap_row",
+ * "logr", "q0".."q7" (the primes).  Returns 0 for an unknown name. */
+uint64_t ephdc_query(const ephdc_ctx* ctx, const char* which);
+
+/* Buffer sizes in bytes. */
+size_t ephdc_sk_bytes(const ephdc_ctx* ctx);          /* secret key (server)          */
+size_t ephdc_galois_key_bytes(const ephdc_ctx* ctx);  /* log2(r) rotation keys         */
+size_t ephdc_model_bytes(const ephdc_ctx* ctx);       /* encrypted class hypervectors */
+size_t ephdc_plain_bytes(const ephdc_ctx* ctx, int32_t B);   /* bfv_encode_plain out  */
+size_t ephdc_out_ct_bytes(const ephdc_ctx* ctx, int32_t B);  /* score ciphertexts     */
+
+/* ---------------------------------------------------------------- server side */
+/* Secret key and Galois (rotation) keys from a 64-bit seed.  Sec. 2.2: RLWE secret
+ * (ternary) and key-switching keys for the rotations of rotate-and-sum, one per
+ * fold step j < log2 r (Galois element 3^(W*2^j) mod 2n), BV decomposition over the
+ * L RNS digits.  Randomness: ChaCha20 (RFC 8439) keyed by the seed.
+ * sk_dev: ephdc_sk_bytes; gk_dev: ephdc_galois_key_bytes (may be NULL if r = 1). */
+ephdc_status bfv_keygen(ephdc_ctx* ctx, uint64_t seed, void* sk_dev, void* gk_dev,
+                        void* stream);
+
+/* Encrypt the k class hypervectors (Sec. 4.1: the model, not the queries, is
+ * encrypted).  class_hv_dev: int8 [k][D] row-major.  Secret-key BFV encryption:
+ * c1 = a, c0 = -a*s + e + floor(q/t)*m per ciphertext, slots laid out per (k_in, r).
+ * model_dev: ephdc_model_bytes, device-private NTT-domain order. */
+ephdc_status bfv_encrypt_model(ephdc_ctx* ctx, const int8_t* class_hv_dev, const void* sk_dev,
+                               uint64_t seed, void* model_dev, void* stream);
+
+/* Decrypt score ciphertexts (checking only; needs the server's secret key).
+ * out_ct_dev: as written by bfv_ptct_similarity / ephdc_infer for a batch of B.
+ * scores_dev: uint32 [B][k], values in [0, t): sum_d h[d] * c_j[d] mod t. */
+ephdc_status bfv_decrypt_scores(ephdc_ctx* ctx, const void* sk_dev, const uint32_t* out_ct_dev,
+                                int32_t B, uint32_t* scores_dev, void* stream);
+
+/* ---------------------------------------------------------------- client hot path */
+/* HDC encoding (Sec. 2.1 random projection) with quantisation (Sec. 5.1):
+ * A = X * Wt^T exactly in int32, H = clamp(floor((A + 2^(s-1)) / 2^s), -2^(b-1),
+ * 2^(b-1)-1).  X_dev: int8 [B][F]; Wt_dev: int8 [D][F] (row d = weights of
+ * dimension d); H_dev: int8 [B][D].  1 <= B <= max_batch. */
+ephdc_status hdc_encode(ephdc_ctx* ctx, const int8_t* X_dev, const int8_t* Wt_dev, int32_t B,
+                        int8_t* H_dev, void* stream);
+
+/* Batch-encode query hypervectors into BFV plaintexts (EncPt): slot packing per
+ * (k_in, r), inverse NTT mod t (slot -> coefficient), centred lift and forward
+ * NTT per RNS limb.  H_dev: int8 [B][D].  pt_dev: ephdc_plain_bytes(B). */
+ephdc_status bfv_encode_plain(ephdc_ctx* ctx, const int8_t* H_dev, int32_t B, uint32_t* pt_dev,
+                              void* stream);
+
+/* Encrypted similarity (HE compute, Sec. 4.1): for every group g and ciphertext
+ * column j', acc = sum_i pt[g][i] * model[i][j'] (pt x ct multiply-accumulate over
+ * the RNS limbs), then log2(r) rotate-and-sum steps with key switching, then the
+ * inverse NTT to the coefficient domain.  out_ct_dev: uint32 [G][k/k_in][2][L][n],
+ * G = ceil(B / cap).  gk_dev may be NULL if r = 1. */
+ephdc_status bfv_ptct_similarity(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t B,
+                                 const void* model_dev, const void* gk_dev, uint32_t* out_ct_dev,
+                                 void* stream);
+
+/* The whole client path in one call: hdc_encode, bfv_encode_plain and
+ * bfv_ptct_similarity on context scratch. */
+ephdc_status ephdc_infer(ephdc_ctx* ctx, const int8_t* X_dev, const int8_t* Wt_dev, int32_t B,
+                         const void* model_dev, const void* gk_dev, uint32_t* out_ct_dev,
+                         void* stream);
+
+/* ---------------------------------------------------------------- host formats */
+/* Copy `count` device NTT-domain ciphertexts (e.g. the model, [2][L][n] each) to
+ * the host in the coefficient domain, uint32 [count][2][L][n].  Synchronous. */
+ephdc_status ephdc_ct_to_host_coeff(ephdc_ctx* ctx, const void* ct_dev, int32_t count,
+                                    uint32_t* host);
+/* The secret key as n signed coefficients in {-1, 0, 1} on the host.  Synchronous. */
+ephdc_status ephdc_sk_to_host(ephdc_ctx* ctx, const void* sk_dev, int32_t* host);
+/* Galois keys to the host, uint32 [log2 r][L digits][2][L limbs][n] coefficient
+ * domain.  Synchronous. */
+ephdc_status ephdc_gk_to_host_coeff(ephdc_ctx* ctx, const void* gk_dev, uint32_t* host);
+/* Plaintexts from bfv_encode_plain to the host as the lifted plaintext polynomial
+ * per limb, uint32 [count][L][n] in [0, q_l).  Synchronous. */
+ephdc_status ephdc_plain_to_host_coeff(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t count,
+                                       uint32_t* host);
+
+/* Forward (inverse = 0) or inverse (inverse = 1) negacyclic NTT of `count`
+ * polynomials mod q_limb (limb = L selects t), in place on the device, with the
+ * evaluation vector in natural order: a_hat[j] = a(psi^(2j+1)).  For checking the
+ * transform against other implementations. */
+ephdc_status ephdc_ntt_natural(ephdc_ctx* ctx, uint32_t limb, uint32_t* poly_dev, int32_t count,
+                               int inverse, void* stream);
+
+/* ---------------------------------------------------------------- measurement */
+/* Stages of the client path, for per-stage device timing. */
+enum {
+  EPHDC_STAGE_HDC = 0,     /* hdc_encode                                   */
+  EPHDC_STAGE_ENCODE = 1,  /* bfv_encode_plain                             */
+  EPHDC_STAGE_MAC = 2,     /* pt x ct multiply-accumulate (+ split reduce) */
+  EPHDC_STAGE_ROTATE = 3,  /* rotate-and-sum with key switching            */
+  EPHDC_STAGE_EXPORT = 4,  /* inverse NTT of the score ciphertexts         */
+  EPHDC_NSTAGES = 5
+};
+/* When on, every client-path call records a CUDA event pair around each stage on the
+ * call's own stream (no synchronisation).  Off by default. */
+ephdc_status ephdc_profile_enable(ephdc_ctx* ctx, int on);
+/* Waits for the recorded events, writes the summed device milliseconds per stage
+ * (ms[EPHDC_NSTAGES]), the number of recorded calls per stage (calls[EPHDC_NSTAGES],
+ * may be NULL) and the number of kernel launches the library has enqueued since the
+ * last read (*launches, may be NULL), then clears the record. */
+ephdc_status ephdc_profile_read(ephdc_ctx* ctx, double* ms, uint64_t* calls, uint64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EPHDC_H */

@@ -1,0 +1,280 @@
+// Internal definitions of the EP-HDC CUDA library (sm_103a).
+//
+// Everything on the path is exact integer arithmetic: residues modulo 30-bit RNS
+// primes q_l = 1 (mod 2n) and modulo t = 65537.  Modular products with a fixed
+// operand (twiddles, key material) use Shoup's precomputed quotient; products of
+// two variable residues accumulate lazily in 64 bits and are reduced once.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ephdc.h"
+
+#define EPHDC_MAXL 8
+#define EPHDC_T 65537u
+#define EPHDC_CDT_LEN 38
+#define EPHDC_BIGW 10  // words of the multi-word integers used by decryption
+
+// One NTT modulus and its tables (device pointers).
+struct ModP {
+  uint32_t p;
+  uint32_t ninv, ninv_sh;  // n^-1 mod p and its Shoup quotient
+  uint64_t mu;             // floor(2^64 / p) for Barrett reduction of 64-bit sums
+  const uint2* tw;         // tw[k]  = (psi^brv(k),  Shoup quotient), k in [1, n)
+  const uint2* itw;        // itw[k] = (psi^-brv(k), Shoup quotient)
+};
+
+// Parameters and tables as seen by kernels (passed by value).
+struct DevCtx {
+  uint32_t n, logn, L, k, k_in, Kp, r, logr, W, cap_row, cap, P, D, F, bits;
+  int32_t shift;
+  ModP mq[EPHDC_MAXL];  // the RNS primes
+  ModP mt;              // t = 65537
+  uint32_t delta[EPHDC_MAXL];  // floor(Q / t) mod q_l
+  uint32_t qhat_inv[EPHDC_MAXL];  // (Q / q_l)^-1 mod q_l
+  uint32_t big_Q[EPHDC_BIGW];     // Q = prod q_l (little-endian 32-bit words)
+  uint32_t big_Qhalf[EPHDC_BIGW]; // floor(Q / 2)
+  uint32_t big_Qhat[EPHDC_MAXL][EPHDC_BIGW];  // Q / q_l
+  const uint32_t* pos2slot;  // device NTT position j -> slot index rho*(n/2) + col
+  const uint32_t* slot2pos;  // slot index -> device NTT position
+  const uint32_t* galois;    // galois[j] = 3^(W*2^j) mod 2n, j < logr
+  uint64_t cdt[EPHDC_CDT_LEN];
+};
+
+// ------------------------------------------------------------------ arithmetic
+__device__ __forceinline__ uint32_t mulshoup(uint32_t x, uint32_t w, uint32_t wsh, uint32_t p) {
+  // x * w mod p in [0, 2p) for any x < 2^32, w < p, wsh = floor(w 2^32 / p)
+  return x * w - __umulhi(x, wsh) * p;
+}
+__device__ __forceinline__ uint32_t csub(uint32_t x, uint32_t p) { return x >= p ? x - p : x; }
+__device__ __forceinline__ uint32_t addm(uint32_t a, uint32_t b, uint32_t p) {
+  return csub(a + b, p);
+}
+__device__ __forceinline__ uint32_t subm(uint32_t a, uint32_t b, uint32_t p) {
+  return a >= b ? a - b : a + p - b;
+}
+// x mod p for any 64-bit x (Barrett with mu = floor(2^64/p)); result in [0, p)
+__device__ __forceinline__ uint32_t red64(uint64_t x, uint32_t p, uint64_t mu) {
+  uint64_t qh = __umul64hi(x, mu);
+  uint32_t r = (uint32_t)(x - qh * p);  // < 3p < 2^32
+  r = csub(r, 2 * p);
+  return csub(r, p);
+}
+__device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, const ModP& m) {
+  return red64((uint64_t)a * b, m.p, m.mu);
+}
+
+// shared-memory index with one pad word per 32 (bank-conflict-free NTT passes)
+__device__ __forceinline__ uint32_t padi(uint32_t i) { return i + (i >> 5); }
+__host__ __device__ constexpr uint32_t padded_words(uint32_t n) { return n + (n >> 5); }
+
+__device__ __forceinline__ uint32_t brev(uint32_t v, uint32_t bits) {
+  return __brev(v) >> (32 - bits);
+}
+
+// ------------------------------------------------------------------ NTT
+// Device NTT order: position j holds a(psi^(2 brv(j) + 1)).  The forward transform
+// is the merged negacyclic Cooley-Tukey network (natural order in, bit-reversed
+// out); the inverse is the Gentleman-Sande mirror.  Stages are grouped into passes
+// of K radix-2 stages held in registers; a thread owns 2^K elements with stride
+// S = n / (m0 2^K), where m0 is the block count at the pass's first stage.  The
+// last pass uses K = 5 with contiguous elements, so every earlier pass has S >= 32
+// and, with one pad word per 32, every pass is bank-conflict-free.
+//
+// Forward butterflies keep values in [0, 4p) (Harvey); the inverse keeps [0, 2p).
+
+template <int K>
+__device__ __forceinline__ void fwd_pass(uint32_t* s, uint32_t logn, uint32_t logm0,
+                                         const uint2* __restrict__ tw, uint32_t p) {
+  const uint32_t logS = logn - logm0 - K;
+  const uint32_t S = 1u << logS;
+  const uint32_t groups = 1u << (logn - K);
+  const uint32_t m0 = 1u << logm0;
+  const uint32_t two_p = 2 * p;
+  for (uint32_t gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+    const uint32_t blk = gi >> logS, j0 = gi & (S - 1);
+    const uint32_t base = (blk << (logS + K)) + j0;
+    uint32_t x[1 << K];
+#pragma unroll
+    for (int e = 0; e < (1 << K); e++) x[e] = s[padi(base + (e << logS))];
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+      const int half = 1 << (K - 1 - r);
+      uint2 w[1 << (K - 1)];
+#pragma unroll
+      for (int u = 0; u < (1 << r); u++) w[u] = __ldg(&tw[((m0 + blk) << r) + u]);
+#pragma unroll
+      for (int e = 0; e < (1 << K); e++) {
+        if (e & half) continue;
+        const uint2 ww = w[e >> (K - r)];
+        uint32_t X = x[e];
+        X = X >= two_p ? X - two_p : X;
+        const uint32_t T = mulshoup(x[e + half], ww.x, ww.y, p);
+        x[e] = X + T;
+        x[e + half] = X - T + two_p;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << K); e++) s[padi(base + (e << logS))] = x[e];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void inv_pass(uint32_t* s, uint32_t logn, uint32_t logm0,
+                                         const uint2* __restrict__ itw, uint32_t p) {
+  const uint32_t logS = logn - logm0 - K;
+  const uint32_t S = 1u << logS;
+  const uint32_t groups = 1u << (logn - K);
+  const uint32_t m0 = 1u << logm0;
+  const uint32_t two_p = 2 * p;
+  for (uint32_t gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+    const uint32_t blk = gi >> logS, j0 = gi & (S - 1);
+    const uint32_t base = (blk << (logS + K)) + j0;
+    uint32_t x[1 << K];
+#pragma unroll
+    for (int e = 0; e < (1 << K); e++) x[e] = s[padi(base + (e << logS))];
+#pragma unroll
+    for (int r = K - 1; r >= 0; r--) {
+      const int half = 1 << (K - 1 - r);
+      uint2 w[1 << (K - 1)];
+#pragma unroll
+      for (int u = 0; u < (1 << r); u++) w[u] = __ldg(&itw[((m0 + blk) << r) + u]);
+#pragma unroll
+      for (int e = 0; e < (1 << K); e++) {
+        if (e & half) continue;
+        const uint2 ww = w[e >> (K - r)];
+        const uint32_t X = x[e], Y = x[e + half];
+        uint32_t U = X + Y;
+        U = U >= two_p ? U - two_p : U;
+        x[e] = U;
+        x[e + half] = mulshoup(X - Y + two_p, ww.x, ww.y, p);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << K); e++) s[padi(base + (e << logS))] = x[e];
+  }
+}
+
+// pass schedule: the last pass has min(5, logn) stages, the earlier ones <= 5
+__device__ __forceinline__ int pass_k(uint32_t logn, int idx, int* npass) {
+  const int last = logn < 5 ? (int)logn : 5;
+  const int rest = (int)logn - last;
+  const int front = (rest + 4) / 5;  // passes before the last
+  *npass = front + 1;
+  if (idx == front) return last;
+  // spread `rest` stages over `front` passes, larger ones first
+  const int base = front ? rest / front : 0, extra = front ? rest % front : 0;
+  return base + (idx < extra ? 1 : 0);
+}
+
+// forward NTT in shared memory (padded layout); input in [0, 4p), output in [0, p)
+static __device__ __noinline__ void ntt_fwd_smem(uint32_t* s, uint32_t logn, const ModP m) {
+  int np;
+  pass_k(logn, 0, &np);
+  uint32_t logm0 = 0;
+  for (int i = 0; i < np; i++) {
+    int K = pass_k(logn, i, &np);
+    switch (K) {
+      case 1: fwd_pass<1>(s, logn, logm0, m.tw, m.p); break;
+      case 2: fwd_pass<2>(s, logn, logm0, m.tw, m.p); break;
+      case 3: fwd_pass<3>(s, logn, logm0, m.tw, m.p); break;
+      case 4: fwd_pass<4>(s, logn, logm0, m.tw, m.p); break;
+      default: fwd_pass<5>(s, logn, logm0, m.tw, m.p); break;
+    }
+    logm0 += K;
+    __syncthreads();
+  }
+  const uint32_t n = 1u << logn;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    uint32_t v = s[padi(i)];
+    v = csub(v, 2 * m.p);
+    s[padi(i)] = csub(v, m.p);
+  }
+  __syncthreads();
+}
+
+// inverse NTT in shared memory; input in [0, 2p), output in [0, p)
+static __device__ __noinline__ void ntt_inv_smem(uint32_t* s, uint32_t logn, const ModP m) {
+  int np;
+  pass_k(logn, 0, &np);
+  uint32_t logm0 = logn;
+  for (int i = np - 1; i >= 0; i--) {
+    int K = pass_k(logn, i, &np);
+    logm0 -= K;
+    switch (K) {
+      case 1: inv_pass<1>(s, logn, logm0, m.itw, m.p); break;
+      case 2: inv_pass<2>(s, logn, logm0, m.itw, m.p); break;
+      case 3: inv_pass<3>(s, logn, logm0, m.itw, m.p); break;
+      case 4: inv_pass<4>(s, logn, logm0, m.itw, m.p); break;
+      default: inv_pass<5>(s, logn, logm0, m.itw, m.p); break;
+    }
+    __syncthreads();
+  }
+  const uint32_t n = 1u << logn;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    uint32_t v = mulshoup(s[padi(i)], m.ninv, m.ninv_sh, m.p);
+    s[padi(i)] = csub(v, m.p);
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ ChaCha20 (RFC 8439)
+__device__ __forceinline__ uint32_t rotl(uint32_t v, int c) { return (v << c) | (v >> (32 - c)); }
+#define EPHDC_QR(a, b, c, d)                 \
+  a += b; d ^= a; d = rotl(d, 16);           \
+  c += d; b ^= c; b = rotl(b, 12);           \
+  a += b; d ^= a; d = rotl(d, 8);            \
+  c += d; b ^= c; b = rotl(b, 7);
+
+// block `counter` of the stream keyed by seed with nonce (domain, obj_hi, obj_lo)
+__device__ __forceinline__ void chacha_block(uint64_t seed, uint32_t domain, uint64_t obj,
+                                             uint32_t counter, uint32_t out[16]) {
+  const uint32_t in[16] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u,
+                           (uint32_t)seed, (uint32_t)(seed >> 32), 0, 0, 0, 0, 0, 0,
+                           counter, domain, (uint32_t)(obj >> 32), (uint32_t)obj};
+  uint32_t x0 = in[0], x1 = in[1], x2 = in[2], x3 = in[3], x4 = in[4], x5 = in[5], x6 = in[6],
+           x7 = in[7], x8 = in[8], x9 = in[9], x10 = in[10], x11 = in[11], x12 = in[12],
+           x13 = in[13], x14 = in[14], x15 = in[15];
+#pragma unroll 1
+  for (int i = 0; i < 10; i++) {
+    EPHDC_QR(x0, x4, x8, x12) EPHDC_QR(x1, x5, x9, x13) EPHDC_QR(x2, x6, x10, x14)
+    EPHDC_QR(x3, x7, x11, x15) EPHDC_QR(x0, x5, x10, x15) EPHDC_QR(x1, x6, x11, x12)
+    EPHDC_QR(x2, x7, x8, x13) EPHDC_QR(x3, x4, x9, x14)
+  }
+  out[0] = x0 + in[0]; out[1] = x1 + in[1]; out[2] = x2 + in[2]; out[3] = x3 + in[3];
+  out[4] = x4 + in[4]; out[5] = x5 + in[5]; out[6] = x6 + in[6]; out[7] = x7 + in[7];
+  out[8] = x8 + in[8]; out[9] = x9 + in[9]; out[10] = x10 + in[10]; out[11] = x11 + in[11];
+  out[12] = x12 + in[12]; out[13] = x13 + in[13]; out[14] = x14 + in[14];
+  out[15] = x15 + in[15];
+}
+
+// ------------------------------------------------------------------ host context
+struct ephdc_ctx_impl;  // defined in host.cu
+
+// launch helpers implemented in the kernel translation units
+namespace ephdc {
+cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt, int B,
+                              int8_t* H, cudaStream_t st);
+cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_t* pt,
+                                cudaStream_t st);
+cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                       uint32_t* partial, int splits, uint32_t* acc, cudaStream_t st);
+cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
+                              int count, const uint32_t* gk, cudaStream_t st);
+cudaError_t launch_export(const DevCtx& c, const uint32_t* acc, int count, uint32_t* out,
+                          cudaStream_t st);
+cudaError_t launch_keygen(const DevCtx& c, uint64_t seed, uint32_t* sk, uint32_t* gk,
+                          cudaStream_t st);
+cudaError_t launch_encrypt_model(const DevCtx& c, const int8_t* classes, const uint32_t* sk,
+                                 uint64_t seed, uint32_t* model, cudaStream_t st);
+cudaError_t launch_decrypt_scores(const DevCtx& c, const uint32_t* sk, const uint32_t* ct,
+                                  int B, uint32_t* xbuf, uint32_t* scores, cudaStream_t st);
+cudaError_t launch_ntt_natural(const DevCtx& c, uint32_t limb, uint32_t* poly, int count,
+                               int inverse, cudaStream_t st);
+cudaError_t launch_to_coeff(const DevCtx& c, const uint32_t* in, uint32_t* out, int count,
+                            int limbs_per_item, int in_stride_words, int limb_stride_words,
+                            int limb0_is_digit_major, cudaStream_t st);
+cudaError_t launch_sk_to_coeff(const DevCtx& c, const uint32_t* sk, int32_t* out, uint32_t* tmp,
+                               cudaStream_t st);
+}  // namespace ephdc

@@ -1,0 +1,680 @@
+// Host side of the EP-HDC CUDA library: parameter derivation, device tables,
+// context and scratch management, and the C-ABI entry points declared in
+// include/ephdc.h.  Every step of the inference path runs in the kernels of
+// k_hdc.cu, k_client.cu and k_server.cu; this file only validates arguments,
+// derives constants and enqueues launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ephdc_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ number theory
+uint32_t pw(uint64_t b, uint64_t e, uint32_t m) {
+  unsigned __int128 r = 1, x = b % m;
+  while (e) {
+    if (e & 1) r = (r * x) % m;
+    x = (x * x) % m;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+// Miller-Rabin with the witnesses {2, 7, 61}, exact for all 32-bit inputs.
+bool prime32(uint32_t v) {
+  if (v < 2) return false;
+  for (uint32_t sp : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+    if (v % sp == 0) return v == sp;
+  uint32_t d = v - 1, s = 0;
+  while (!(d & 1)) d >>= 1, s++;
+  for (uint32_t a : {2u, 7u, 61u}) {
+    uint64_t x = pw(a, d, v);
+    if (x == 1 || x == v - 1) continue;
+    bool witness = true;
+    for (uint32_t i = 1; i < s && witness; i++) {
+      x = (x * x) % v;
+      if (x == v - 1) witness = false;
+    }
+    if (witness) return false;
+  }
+  return true;
+}
+
+uint32_t brv_host(uint32_t v, uint32_t bits) {
+  uint32_t r = 0;
+  for (uint32_t i = 0; i < bits; i++) r |= ((v >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+
+// primitive 2n-th root: x^((p-1)/2n) for the least quadratic non-residue x
+uint32_t root2n(uint32_t p, uint32_t n) {
+  uint32_t x = 2;
+  while (pw(x, (p - 1) / 2, p) != p - 1) x++;
+  return pw(x, (p - 1) / (2ull * n), p);
+}
+
+uint32_t shoup(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+
+// little-endian multi-word helpers (host)
+void bmul(uint32_t* a, uint32_t m) {
+  uint64_t c = 0;
+  for (int i = 0; i < EPHDC_BIGW; i++) {
+    uint64_t v = (uint64_t)a[i] * m + c;
+    a[i] = (uint32_t)v;
+    c = v >> 32;
+  }
+}
+uint32_t bdiv(uint32_t* a, uint32_t d) {  // a /= d, returns remainder
+  uint64_t r = 0;
+  for (int i = EPHDC_BIGW - 1; i >= 0; i--) {
+    uint64_t cur = (r << 32) | a[i];
+    a[i] = (uint32_t)(cur / d);
+    r = cur % d;
+  }
+  return (uint32_t)r;
+}
+uint32_t bmod(const uint32_t* a, uint32_t d) {
+  uint64_t r = 0;
+  for (int i = EPHDC_BIGW - 1; i >= 0; i--) r = ((r << 32) | a[i]) % d;
+  return (uint32_t)r;
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+struct ephdc_ctx {
+  ephdc_params prm;
+  DevCtx dc;
+  int device = 0;
+  std::string err;
+  // device allocations owned by the context
+  void* tables = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  int G_max = 0, splits = 1;
+  // scratch sub-buffers
+  int8_t* H = nullptr;
+  uint32_t* pt = nullptr;
+  uint32_t* partial = nullptr;
+  uint32_t* acc = nullptr;
+  uint32_t* tmp = nullptr;
+  uint32_t* digits = nullptr;
+  // per-stage device timing (ephdc_profile_enable / ephdc_profile_read)
+  struct Rec {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  uint64_t launches = 0;
+};
+
+static cudaEvent_t take_event(ephdc_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// RAII bracket: records an event pair around one stage on the call's stream
+struct StageTimer {
+  ephdc_ctx* c;
+  cudaStream_t st;
+  ephdc_ctx::Rec r{};
+  StageTimer(ephdc_ctx* c_, int stage, cudaStream_t st_, uint64_t nlaunch) : c(c_), st(st_) {
+    c->launches += nlaunch;
+    if (!c->prof) return;
+    r.stage = stage;
+    r.a = take_event(c);
+    r.b = take_event(c);
+    cudaEventRecord(r.a, st);
+  }
+  ~StageTimer() {
+    if (!c->prof) return;
+    cudaEventRecord(r.b, st);
+    c->recs.push_back(r);
+  }
+};
+
+static ephdc_status fail(ephdc_ctx* c, ephdc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+static ephdc_status cuda_status(ephdc_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return EPHDC_OK;
+  return fail(c, EPHDC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static uint32_t groups_for(const ephdc_ctx* c, int32_t B) {
+  return (uint32_t)((B + c->dc.cap - 1) / c->dc.cap);
+}
+
+static int mac_splits(const DevCtx& dc, int G) {
+  // enough (limb, quad, split) threads to fill every SM a few times over
+  long per_split = (long)dc.L * (dc.n / 4) * G;
+  long want = 152L * 2048;
+  long s = (want + per_split - 1) / per_split;
+  if (s < 1) s = 1;
+  if (s > (long)dc.P) s = dc.P;
+  if (s > 64) s = 64;
+  return (int)s;
+}
+
+extern "C" {
+
+ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
+  if (!out) return fail(nullptr, EPHDC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(nullptr, EPHDC_EINVAL, "params is NULL");
+  const uint32_t n = p->n;
+  if (n < 1024 || n > 16384 || (n & (n - 1)))
+    return fail(nullptr, EPHDC_EINVAL, "n must be a power of two in [1024, 16384], got %u", n);
+  if (p->L < 2 || p->L > EPHDC_MAXL)
+    return fail(nullptr, EPHDC_EINVAL, "L must be in [2, %d], got %u", EPHDC_MAXL, p->L);
+  if (p->k < 1 || p->k_in < 1 || p->k % p->k_in)
+    return fail(nullptr, EPHDC_EINVAL, "k_in must divide k (k=%u, k_in=%u)", p->k, p->k_in);
+  if (p->r < 1 || (p->r & (p->r - 1)) || p->r > n / (2 * p->k_in))
+    return fail(nullptr, EPHDC_EINVAL, "r must be a power of two <= n/(2 k_in), got %u", p->r);
+  if (p->D < 1) return fail(nullptr, EPHDC_EINVAL, "D must be positive");
+  if (p->F < 16 || p->F % 16) return fail(nullptr, EPHDC_EINVAL, "F must be a positive multiple of 16");
+  if (p->hv_bits < 2 || p->hv_bits > 8) return fail(nullptr, EPHDC_EINVAL, "hv_bits must be in [2, 8]");
+  if (p->shift < 0 || p->shift > 30) return fail(nullptr, EPHDC_EINVAL, "shift must be in [0, 30]");
+  if (p->max_batch < 1) return fail(nullptr, EPHDC_EINVAL, "max_batch must be positive");
+  if (!(p->sigma > 0.0 && p->sigma < 100.0)) return fail(nullptr, EPHDC_EINVAL, "sigma out of range");
+
+  ephdc_ctx* c = new ephdc_ctx();
+  c->prm = *p;
+  DevCtx& d = c->dc;
+  memset(&d, 0, sizeof d);
+  d.n = n;
+  d.logn = 0;
+  while ((1u << d.logn) < n) d.logn++;
+  d.L = p->L; d.k = p->k; d.k_in = p->k_in; d.Kp = p->k / p->k_in; d.r = p->r;
+  d.logr = 0;
+  while ((1u << d.logr) < p->r) d.logr++;
+  d.W = n / (2 * p->r);
+  d.cap_row = d.W / p->k_in;
+  d.cap = 2 * d.cap_row;
+  d.P = (p->D + p->r - 1) / p->r;
+  d.D = p->D; d.F = p->F; d.bits = p->hv_bits; d.shift = p->shift;
+
+  // the L largest primes q < 2^30 with q = 1 (mod 2n)
+  std::vector<uint32_t> q;
+  for (uint64_t j = 1; q.size() < p->L; j++) {
+    uint64_t cand = (1ull << 30) - j * 2ull * n + 1;
+    if (cand < (1ull << 29)) {
+      delete c;
+      return fail(nullptr, EPHDC_EINVAL, "not enough NTT primes");
+    }
+    if (prime32((uint32_t)cand)) q.push_back((uint32_t)cand);
+  }
+
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, EPHDC_ECUDA, "no CUDA device");
+  }
+
+  // tables: twiddles for L primes + t (2 x n uint2 each), slot maps, Galois elements
+  const int nm = p->L + 1;
+  size_t tw_bytes = (size_t)nm * 2 * n * sizeof(uint2);
+  size_t map_bytes = 2 * (size_t)n * sizeof(uint32_t);
+  size_t gal_bytes = 64 * sizeof(uint32_t);
+  size_t total = align256(tw_bytes) + align256(map_bytes) + align256(gal_bytes);
+  std::vector<uint8_t> host(total, 0);
+  uint2* htw = (uint2*)host.data();
+  uint32_t* hmap = (uint32_t*)(host.data() + align256(tw_bytes));
+  uint32_t* hgal = (uint32_t*)(host.data() + align256(tw_bytes) + align256(map_bytes));
+
+  if (cudaMalloc(&c->tables, total) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, EPHDC_ENOMEM, "cudaMalloc of %zu table bytes failed", total);
+  }
+  uint2* dtw = (uint2*)c->tables;
+  for (int mi = 0; mi < nm; mi++) {
+    const uint32_t pm = mi < (int)p->L ? q[mi] : EPHDC_T;
+    const uint32_t psi = root2n(pm, n), psi_inv = pw(psi, pm - 2, pm);
+    uint2* f = htw + (size_t)mi * 2 * n;
+    uint2* b = f + n;
+    for (uint32_t k = 0; k < n; k++) {
+      uint32_t e = brv_host(k, d.logn);
+      uint32_t w = pw(psi, e, pm), wi = pw(psi_inv, e, pm);
+      f[k] = make_uint2(w, shoup(w, pm));
+      b[k] = make_uint2(wi, shoup(wi, pm));
+    }
+    ModP mp;
+    mp.p = pm;
+    mp.ninv = pw(n, pm - 2, pm);
+    mp.ninv_sh = shoup(mp.ninv, pm);
+    mp.mu = (uint64_t)(((unsigned __int128)1 << 64) / pm);
+    mp.tw = dtw + (size_t)mi * 2 * n;
+    mp.itw = mp.tw + n;
+    if (mi < (int)p->L) d.mq[mi] = mp;
+    else d.mt = mp;
+  }
+  // slots: slot index rho*(n/2) + col has exponent e = 3^col (rho = 0) or 2n - 3^col
+  // (rho = 1); the device position with exponent e is brv((e - 1) / 2)
+  uint32_t* s2p = hmap;
+  uint32_t* p2s = hmap + n;
+  for (uint32_t rho = 0; rho < 2; rho++)
+    for (uint32_t col = 0; col < n / 2; col++) {
+      uint32_t e = pw(3, col, 2 * n);
+      if (rho) e = 2 * n - e;
+      uint32_t pos = brv_host((e - 1) / 2, d.logn);
+      uint32_t sidx = rho * (n / 2) + col;
+      s2p[sidx] = pos;
+      p2s[pos] = sidx;
+    }
+  for (uint32_t j = 0; j < d.logr; j++) hgal[j] = pw(3, (uint64_t)d.W << j, 2 * n);
+  d.slot2pos = (const uint32_t*)((uint8_t*)c->tables + align256(tw_bytes));
+  d.pos2slot = d.slot2pos + n;
+  d.galois = (const uint32_t*)((uint8_t*)c->tables + align256(tw_bytes) + align256(map_bytes));
+  cudaError_t ce = cudaMemcpy(c->tables, host.data(), total, cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(c->tables);
+    delete c;
+    return fail(nullptr, EPHDC_ECUDA, "table upload: %s", cudaGetErrorString(ce));
+  }
+
+  // Q, floor(Q/t) mod q_l, CRT constants
+  uint32_t Qw[EPHDC_BIGW] = {1};
+  for (uint32_t l = 0; l < p->L; l++) bmul(Qw, q[l]);
+  memcpy(d.big_Q, Qw, sizeof Qw);
+  uint32_t Qt[EPHDC_BIGW];
+  memcpy(Qt, Qw, sizeof Qw);
+  bdiv(Qt, EPHDC_T);
+  uint32_t Qh[EPHDC_BIGW];
+  memcpy(Qh, Qw, sizeof Qw);
+  bdiv(Qh, 2);
+  memcpy(d.big_Qhalf, Qh, sizeof Qh);
+  for (uint32_t l = 0; l < p->L; l++) {
+    d.delta[l] = bmod(Qt, q[l]);
+    uint32_t hat[EPHDC_BIGW] = {1};
+    for (uint32_t o = 0; o < p->L; o++)
+      if (o != l) bmul(hat, q[o]);
+    memcpy(d.big_Qhat[l], hat, sizeof hat);
+    d.qhat_inv[l] = pw(bmod(hat, q[l]), q[l] - 2, q[l]);
+  }
+  // discrete Gaussian table: T[m] = floor(2^64 P(X <= -19 + m)), weights
+  // exp(-x^2 / (2 sigma^2)) on [-19, 19]
+  {
+    double wgt[2 * 19 + 1], tot = 0.0;
+    const double den = 2.0 * p->sigma * p->sigma;
+    for (int x = -19; x <= 19; x++) {
+      double xx = (double)x * (double)x;
+      wgt[x + 19] = std::exp(-(xx / den));
+    }
+    for (int i = 0; i <= 38; i++) tot += wgt[i];
+    double cum = 0.0;
+    for (int i = 0; i < EPHDC_CDT_LEN; i++) {
+      cum += wgt[i];
+      d.cdt[i] = (uint64_t)std::ldexp(cum / tot, 64);
+    }
+  }
+
+  // scratch for batches up to max_batch
+  c->G_max = (int)groups_for(c, (int32_t)p->max_batch);
+  c->splits = mac_splits(d, 1);
+  const size_t poly = (size_t)n * sizeof(uint32_t);
+  const size_t acc_bytes = (size_t)c->G_max * d.Kp * 2 * d.L * poly;
+  // split partial sums: the largest splits(G) * G over the batch sizes allowed
+  size_t part_groups = 0;
+  for (int G = 1; G <= c->G_max; G++) {
+    size_t v = (size_t)mac_splits(d, G) * G;
+    if (v > part_groups) part_groups = v;
+  }
+  size_t off = 0;
+  size_t oH = off; off += align256((size_t)p->max_batch * p->D);
+  size_t opt = off; off += align256((size_t)c->G_max * d.P * d.L * poly);
+  size_t opart = off; off += align256(part_groups * d.Kp * 2 * d.L * poly);
+  size_t oacc = off; off += align256(acc_bytes);
+  size_t otmp = off; off += align256(acc_bytes);
+  size_t odig = off; off += align256((size_t)c->G_max * d.Kp * d.L * poly);
+  c->scratch_bytes = off;
+  if (cudaMalloc(&c->scratch, off) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->tables);
+    delete c;
+    return fail(nullptr, EPHDC_ENOMEM, "cudaMalloc of %zu scratch bytes failed", off);
+  }
+  uint8_t* sb = (uint8_t*)c->scratch;
+  c->H = (int8_t*)(sb + oH);
+  c->pt = (uint32_t*)(sb + opt);
+  c->partial = (uint32_t*)(sb + opart);
+  c->acc = (uint32_t*)(sb + oacc);
+  c->tmp = (uint32_t*)(sb + otmp);
+  c->digits = (uint32_t*)(sb + odig);
+  *out = c;
+  return EPHDC_OK;
+}
+
+void ephdc_ctx_destroy(ephdc_ctx* c) {
+  if (!c) return;
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->tables) cudaFree(c->tables);
+  delete c;
+}
+
+const char* ephdc_last_error(const ephdc_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+uint64_t ephdc_query(const ephdc_ctx* c, const char* w) {
+  if (!c || !w) return 0;
+  const DevCtx& d = c->dc;
+  if (!strcmp(w, "cap")) return d.cap;
+  if (!strcmp(w, "P")) return d.P;
+  if (!strcmp(w, "Kp")) return d.Kp;
+  if (!strcmp(w, "W")) return d.W;
+  if (!strcmp(w, "cap_row")) return d.cap_row;
+  if (!strcmp(w, "logr")) return d.logr;
+  if (!strcmp(w, "splits")) return (uint64_t)c->splits;
+  if (!strcmp(w, "scratch_bytes")) return c->scratch_bytes;
+  if (w[0] == 'q' && w[1] >= '0' && w[1] <= '7' && w[2] == 0) {
+    uint32_t l = (uint32_t)(w[1] - '0');
+    return l < d.L ? d.mq[l].p : 0;
+  }
+  return 0;
+}
+
+size_t ephdc_sk_bytes(const ephdc_ctx* c) {
+  return c ? (size_t)c->dc.L * c->dc.n * sizeof(uint32_t) : 0;
+}
+size_t ephdc_galois_key_bytes(const ephdc_ctx* c) {
+  return c ? (size_t)c->dc.logr * c->dc.L * c->dc.L * 4 * c->dc.n * sizeof(uint32_t) : 0;
+}
+size_t ephdc_model_bytes(const ephdc_ctx* c) {
+  return c ? (size_t)c->dc.P * c->dc.Kp * 2 * c->dc.L * c->dc.n * sizeof(uint32_t) : 0;
+}
+size_t ephdc_plain_bytes(const ephdc_ctx* c, int32_t B) {
+  if (!c || B < 1) return 0;
+  return (size_t)groups_for(c, B) * c->dc.P * c->dc.L * c->dc.n * sizeof(uint32_t);
+}
+size_t ephdc_out_ct_bytes(const ephdc_ctx* c, int32_t B) {
+  if (!c || B < 1) return 0;
+  return (size_t)groups_for(c, B) * c->dc.Kp * 2 * c->dc.L * c->dc.n * sizeof(uint32_t);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ argument checks
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+#define CHECK_CTX(c)                                                \
+  do {                                                              \
+    if (!(c)) return EPHDC_EINVAL;                                  \
+    (c)->err.clear();                                               \
+  } while (0)
+#define CHECK_PTR(c, ptr, name)                                                   \
+  do {                                                                            \
+    if (!(ptr)) return fail(c, EPHDC_EINVAL, "%s is NULL", name);                 \
+    if (!aligned16(ptr)) return fail(c, EPHDC_EINVAL, "%s is not 16-byte aligned", name); \
+  } while (0)
+#define CHECK_B(c, B)                                                                  \
+  do {                                                                                 \
+    if ((B) < 1 || (uint32_t)(B) > (c)->prm.max_batch)                                 \
+      return fail(c, (B) < 1 ? EPHDC_EINVAL : EPHDC_ENOMEM,                            \
+                  "batch %d outside [1, max_batch=%u]", (int)(B), (c)->prm.max_batch); \
+  } while (0)
+
+static ephdc_status launched(ephdc_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return cuda_status(c, e, what);
+}
+
+static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
+                                    const void* model, const void* gk, uint32_t* out,
+                                    cudaStream_t st) {
+  const DevCtx& d = c->dc;
+  const int G = (int)groups_for(c, B);
+  cudaError_t e;
+  {
+    StageTimer tm(c, EPHDC_STAGE_MAC, st, (2 * d.Kp + 3) / 4 + 1);
+    e = ephdc::launch_mac(d, pt, G, (const uint32_t*)model, c->partial, c->splits, c->acc, st);
+  }
+  if (e != cudaSuccess) return launched(c, e, "ptct_mac");
+  const int count = G * (int)d.Kp;
+  uint32_t* cur = c->acc;
+  if (d.logr) {
+    {
+      StageTimer tm(c, EPHDC_STAGE_ROTATE, st, 2 * d.logr);
+      e = ephdc::launch_rotate_sum(d, c->acc, c->tmp, c->digits, count, (const uint32_t*)gk, st);
+    }
+    if (e != cudaSuccess) return launched(c, e, "rotate_sum");
+    if (d.logr & 1) cur = c->tmp;  // ping-pong: odd number of steps ends in tmp
+  }
+  {
+    StageTimer tm(c, EPHDC_STAGE_EXPORT, st, 1);
+    e = ephdc::launch_export(d, cur, count, out, st);
+  }
+  return launched(c, e, "export");
+}
+
+extern "C" {
+
+ephdc_status bfv_keygen(ephdc_ctx* c, uint64_t seed, void* sk, void* gk, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, sk, "sk_dev");
+  if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
+  return launched(c, ephdc::launch_keygen(c->dc, seed, (uint32_t*)sk, (uint32_t*)gk,
+                                          (cudaStream_t)stream), "keygen");
+}
+
+ephdc_status bfv_encrypt_model(ephdc_ctx* c, const int8_t* classes, const void* sk, uint64_t seed,
+                               void* model, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, classes, "class_hv_dev");
+  CHECK_PTR(c, sk, "sk_dev");
+  CHECK_PTR(c, model, "model_dev");
+  return launched(c, ephdc::launch_encrypt_model(c->dc, classes, (const uint32_t*)sk, seed,
+                                                 (uint32_t*)model, (cudaStream_t)stream),
+                  "encrypt_model");
+}
+
+ephdc_status bfv_decrypt_scores(ephdc_ctx* c, const void* sk, const uint32_t* out_ct, int32_t B,
+                                uint32_t* scores, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, sk, "sk_dev");
+  CHECK_PTR(c, out_ct, "out_ct_dev");
+  CHECK_PTR(c, scores, "scores_dev");
+  CHECK_B(c, B);
+  return launched(c, ephdc::launch_decrypt_scores(c->dc, (const uint32_t*)sk, out_ct, B,
+                                                  c->digits, scores, (cudaStream_t)stream),
+                  "decrypt_scores");
+}
+
+ephdc_status hdc_encode(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_t B, int8_t* H,
+                        void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, X, "X_dev");
+  CHECK_PTR(c, Wt, "Wt_dev");
+  CHECK_PTR(c, H, "H_dev");
+  CHECK_B(c, B);
+  cudaError_t e;
+  {
+    StageTimer tm(c, EPHDC_STAGE_HDC, (cudaStream_t)stream, 1);
+    e = ephdc::launch_hdc_encode(c->dc, X, Wt, B, H, (cudaStream_t)stream);
+  }
+  return launched(c, e, "hdc_encode");
+}
+
+ephdc_status bfv_encode_plain(ephdc_ctx* c, const int8_t* H, int32_t B, uint32_t* pt,
+                              void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, H, "H_dev");
+  CHECK_PTR(c, pt, "pt_dev");
+  CHECK_B(c, B);
+  cudaError_t e;
+  {
+    StageTimer tm(c, EPHDC_STAGE_ENCODE, (cudaStream_t)stream, 1);
+    e = ephdc::launch_encode_plain(c->dc, H, B, pt, (cudaStream_t)stream);
+  }
+  return launched(c, e, "encode_plain");
+}
+
+ephdc_status bfv_ptct_similarity(ephdc_ctx* c, const uint32_t* pt, int32_t B, const void* model,
+                                 const void* gk, uint32_t* out, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, pt, "pt_dev");
+  CHECK_PTR(c, model, "model_dev");
+  CHECK_PTR(c, out, "out_ct_dev");
+  if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
+  CHECK_B(c, B);
+  return similarity_impl(c, pt, B, model, gk, out, (cudaStream_t)stream);
+}
+
+ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_t B,
+                         const void* model, const void* gk, uint32_t* out, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, X, "X_dev");
+  CHECK_PTR(c, Wt, "Wt_dev");
+  CHECK_PTR(c, model, "model_dev");
+  CHECK_PTR(c, out, "out_ct_dev");
+  if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
+  CHECK_B(c, B);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  {
+    StageTimer tm(c, EPHDC_STAGE_HDC, st, 1);
+    e = ephdc::launch_hdc_encode(c->dc, X, Wt, B, c->H, st);
+  }
+  if (e != cudaSuccess) return launched(c, e, "hdc_encode");
+  {
+    StageTimer tm(c, EPHDC_STAGE_ENCODE, st, 1);
+    e = ephdc::launch_encode_plain(c->dc, c->H, B, c->pt, st);
+  }
+  if (e != cudaSuccess) return launched(c, e, "encode_plain");
+  return similarity_impl(c, c->pt, B, model, gk, out, st);
+}
+
+ephdc_status ephdc_ct_to_host_coeff(ephdc_ctx* c, const void* ct, int32_t count, uint32_t* host) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, ct, "ct_dev");
+  if (!host || count < 1) return fail(c, EPHDC_EINVAL, "bad host buffer or count");
+  const DevCtx& d = c->dc;
+  const size_t words = (size_t)count * 2 * d.L * d.n;
+  uint32_t* tmp = nullptr;
+  if (cudaMalloc(&tmp, words * 4) != cudaSuccess) return fail(c, EPHDC_ENOMEM, "cudaMalloc");
+  cudaError_t e = ephdc::launch_to_coeff(d, (const uint32_t*)ct, tmp, count, 2,
+                                         (int)(2 * d.L * d.n), (int)d.n, 0, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host, tmp, words * 4, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  return cuda_status(c, e, "ct_to_host_coeff");
+}
+
+ephdc_status ephdc_gk_to_host_coeff(ephdc_ctx* c, const void* gk, uint32_t* host) {
+  CHECK_CTX(c);
+  const DevCtx& d = c->dc;
+  if (!d.logr) return EPHDC_OK;
+  CHECK_PTR(c, gk, "gk_dev");
+  if (!host) return fail(c, EPHDC_EINVAL, "host is NULL");
+  const int count = (int)(d.logr * d.L);
+  const size_t words = (size_t)count * 2 * d.L * d.n;
+  uint32_t* tmp = nullptr;
+  if (cudaMalloc(&tmp, words * 4) != cudaSuccess) return fail(c, EPHDC_ENOMEM, "cudaMalloc");
+  cudaError_t e = ephdc::launch_to_coeff(d, (const uint32_t*)gk, tmp, count, 2,
+                                         (int)(d.L * 4 * d.n), (int)(4 * d.n), 1, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host, tmp, words * 4, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  return cuda_status(c, e, "gk_to_host_coeff");
+}
+
+ephdc_status ephdc_plain_to_host_coeff(ephdc_ctx* c, const uint32_t* pt, int32_t count,
+                                       uint32_t* host) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, pt, "pt_dev");
+  if (!host || count < 1) return fail(c, EPHDC_EINVAL, "bad host buffer or count");
+  const DevCtx& d = c->dc;
+  const size_t words = (size_t)count * d.L * d.n;
+  uint32_t* tmp = nullptr;
+  if (cudaMalloc(&tmp, words * 4) != cudaSuccess) return fail(c, EPHDC_ENOMEM, "cudaMalloc");
+  cudaError_t e = ephdc::launch_to_coeff(d, pt, tmp, count, 1, (int)(d.L * d.n), (int)d.n, 0, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host, tmp, words * 4, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  return cuda_status(c, e, "plain_to_host_coeff");
+}
+
+ephdc_status ephdc_sk_to_host(ephdc_ctx* c, const void* sk, int32_t* host) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, sk, "sk_dev");
+  if (!host) return fail(c, EPHDC_EINVAL, "host is NULL");
+  const DevCtx& d = c->dc;
+  int32_t* tmp = nullptr;
+  uint32_t* work = nullptr;
+  if (cudaMalloc(&tmp, d.n * 4) != cudaSuccess) return fail(c, EPHDC_ENOMEM, "cudaMalloc");
+  if (cudaMalloc(&work, d.n * 4) != cudaSuccess) {
+    cudaFree(tmp);
+    return fail(c, EPHDC_ENOMEM, "cudaMalloc");
+  }
+  cudaError_t e = ephdc::launch_sk_to_coeff(d, (const uint32_t*)sk, tmp, work, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host, tmp, d.n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  cudaFree(work);
+  return cuda_status(c, e, "sk_to_host");
+}
+
+ephdc_status ephdc_ntt_natural(ephdc_ctx* c, uint32_t limb, uint32_t* poly, int32_t count,
+                               int inverse, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, poly, "poly_dev");
+  if (limb > c->dc.L || count < 1) return fail(c, EPHDC_EINVAL, "bad limb or count");
+  return launched(c, ephdc::launch_ntt_natural(c->dc, limb, poly, count, inverse,
+                                               (cudaStream_t)stream), "ntt_natural");
+}
+
+ephdc_status ephdc_profile_enable(ephdc_ctx* c, int on) {
+  CHECK_CTX(c);
+  c->prof = on != 0;
+  return EPHDC_OK;
+}
+
+ephdc_status ephdc_profile_read(ephdc_ctx* c, double* ms, uint64_t* calls, uint64_t* launches) {
+  CHECK_CTX(c);
+  if (!ms) return fail(c, EPHDC_EINVAL, "ms is NULL");
+  for (int i = 0; i < EPHDC_NSTAGES; i++) {
+    ms[i] = 0.0;
+    if (calls) calls[i] = 0;
+  }
+  cudaError_t err = cudaSuccess;
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    ms[r.stage] += t;
+    if (calls) calls[r.stage]++;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  if (launches) *launches = c->launches;
+  c->launches = 0;
+  return cuda_status(c, err, "profile_read");
+}
+
+}  // extern "C"

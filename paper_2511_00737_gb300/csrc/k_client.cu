@@ -1,0 +1,313 @@
+// Client-side hot path kernels (Sec. 3, Sec. 4.1):
+//   encode_plain  slot packing of query hypervectors + inverse NTT mod t (BFV batch
+//                 encoding, EncPt) + centred lift + forward NTT per RNS limb
+//   mac           plaintext x ciphertext multiply-accumulate over the plaintexts
+//                 (HE compute): streams the NTT-domain encrypted model from HBM
+//   rotate_sum    log2(r) Galois rotations with BV key switching, each added back
+//   export        inverse NTT of the score ciphertexts to the coefficient domain
+#include "ephdc_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t logn) {
+  // device position holding exponent e_j * g (mod 2n), e_j = 2 brv(j) + 1
+  const uint32_t n2mask = (2u << logn) - 1;
+  const uint32_t e = 2 * brev(j, logn) + 1;
+  const uint32_t eg = (e * g) & n2mask;
+  return brev((eg - 1) >> 1, logn);
+}
+
+// ------------------------------------------------------------------ EncPt
+// One CTA per plaintext (g, i).  Query beta = g*cap + rho*cap_row + qq, dimension
+// d = i*r + ch lands in slot (rho, ch*W + jin*cap_row + qq) for every jin < k_in.
+__global__ void __launch_bounds__(512) k_encode_plain(DevCtx c, const int8_t* __restrict__ H,
+                                                      int B, uint32_t* __restrict__ pt) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* mb = sm;
+  uint32_t* wb = sm + padded_words(c.n);
+  const uint32_t gi = blockIdx.x;
+  const uint32_t g = gi / c.P, i = gi - g * c.P;
+  const uint32_t half = c.n >> 1;
+  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
+    const uint32_t sidx = __ldg(&c.pos2slot[j]);
+    const uint32_t rho = sidx >= half;
+    const uint32_t col = sidx - rho * half;
+    const uint32_t ch = col / c.W, within = col - ch * c.W;
+    const uint32_t jin = within / c.cap_row, qq = within - jin * c.cap_row;
+    uint32_t v = 0;
+    if (jin < c.k_in) {
+      const uint32_t d = i * c.r + ch;
+      const uint64_t beta = (uint64_t)g * c.cap + rho * c.cap_row + qq;
+      if (d < c.D && beta < (uint64_t)B) {
+        const int h = H[beta * c.D + d];
+        v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
+      }
+    }
+    mb[padi(j)] = v;
+  }
+  __syncthreads();
+  ntt_inv_smem(mb, c.logn, c.mt);  // slots -> plaintext coefficients in [0, t)
+  const uint32_t thalf = (EPHDC_T - 1) / 2;
+  for (uint32_t l = 0; l < c.L; l++) {
+    const uint32_t p = c.mq[l].p;
+    for (uint32_t kk = threadIdx.x; kk < c.n; kk += blockDim.x) {
+      const uint32_t m = mb[padi(kk)];
+      wb[padi(kk)] = m <= thalf ? m : m + p - EPHDC_T;  // centred lift
+    }
+    __syncthreads();
+    ntt_fwd_smem(wb, c.logn, c.mq[l]);
+    uint32_t* dst = pt + ((size_t)gi * c.L + l) * c.n;
+    for (uint32_t kk = threadIdx.x * 4; kk < c.n; kk += blockDim.x * 4) {
+      uint4 v = make_uint4(wb[padi(kk)], wb[padi(kk + 1)], wb[padi(kk + 2)], wb[padi(kk + 3)]);
+      *reinterpret_cast<uint4*>(dst + kk) = v;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ MAC
+// partial[split][g][o][l][n] = sum_{i in split} pt[g][i][l] * model[i][o][l]  (mod q_l),
+// o = jp*2 + poly.  A thread owns 4 consecutive coefficients of one limb and OC
+// outputs; products (< 2^60) accumulate in 64 bits, reduced every 15 terms.
+template <int OC>
+__global__ void __launch_bounds__(256) k_mac(DevCtx c, const uint32_t* __restrict__ pt,
+                                             const uint32_t* __restrict__ model,
+                                             uint32_t* __restrict__ partial, int G, int splits,
+                                             int o0, int nout) {
+  const uint32_t quads = c.n >> 2;
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= c.L * quads) return;
+  const uint32_t l = tid / quads, quad = tid - l * quads;
+  const uint32_t g = blockIdx.y, split = blockIdx.z;
+  const uint32_t per = (c.P + splits - 1) / splits;
+  const uint32_t i0 = split * per, i1 = min(c.P, i0 + per);
+  const uint32_t p = c.mq[l].p;
+  const uint64_t mu = c.mq[l].mu;
+  const uint32_t O = 2 * c.Kp;
+  uint64_t acc[OC][4];
+#pragma unroll
+  for (int o = 0; o < OC; o++)
+#pragma unroll
+    for (int e = 0; e < 4; e++) acc[o][e] = 0;
+  const uint4* ptp = reinterpret_cast<const uint4*>(pt + (((size_t)g * c.P) * c.L + l) * c.n) + quad;
+  const size_t pt_step = (size_t)c.L * quads;  // uint4 per plaintext
+  const uint4* mp = reinterpret_cast<const uint4*>(model + (size_t)l * c.n) + quad;
+  const size_t out_step = (size_t)c.L * quads;    // uint4 per (ct, poly)
+  const size_t i_step = (size_t)O * out_step;      // uint4 per plaintext index
+  uint32_t cnt = 0;
+  for (uint32_t i = i0; i < i1; i++) {
+    const uint4 a = __ldg(ptp + (size_t)i * pt_step);
+#pragma unroll
+    for (int o = 0; o < OC; o++) {
+      if (o < nout) {
+        const uint4 b = __ldg(mp + (size_t)i * i_step + (size_t)(o0 + o) * out_step);
+        acc[o][0] += (uint64_t)a.x * b.x;
+        acc[o][1] += (uint64_t)a.y * b.y;
+        acc[o][2] += (uint64_t)a.z * b.z;
+        acc[o][3] += (uint64_t)a.w * b.w;
+      }
+    }
+    if (++cnt == 15) {
+      cnt = 0;
+#pragma unroll
+      for (int o = 0; o < OC; o++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[o][e] = red64(acc[o][e], p, mu);
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < OC; o++) {
+    if (o < nout) {
+      uint4 v = make_uint4(red64(acc[o][0], p, mu), red64(acc[o][1], p, mu),
+                           red64(acc[o][2], p, mu), red64(acc[o][3], p, mu));
+      uint4* dst = reinterpret_cast<uint4*>(
+          partial + ((((size_t)split * G + g) * O + (o0 + o)) * c.L + l) * c.n) + quad;
+      *dst = v;
+    }
+  }
+}
+
+// acc[x] = sum_split partial[split][x] mod q_l, x over G*O*L*n words
+__global__ void k_mac_reduce(DevCtx c, const uint32_t* __restrict__ partial, int splits,
+                             size_t words, uint32_t* __restrict__ acc) {
+  const size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= words) return;
+  const uint32_t l = (uint32_t)((x >> c.logn) % c.L);
+  uint64_t s = 0;
+  for (int k = 0; k < splits; k++) s += __ldg(partial + (size_t)k * words + x);
+  acc[x] = red64(s, c.mq[l].p, c.mq[l].mu);
+}
+
+// ------------------------------------------------------------------ rotations
+// digits[ct][i][:] = INTT_{q_i}(tau_g(c1 limb i)): the RNS digits of the rotated c1
+// as integer polynomials with coefficients in [0, q_i).
+__global__ void __launch_bounds__(512) k_ks_digits(DevCtx c, const uint32_t* __restrict__ acc,
+                                                   uint32_t* __restrict__ digits, uint32_t gal) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t ct = blockIdx.x, i = blockIdx.y;
+  const uint32_t* src = acc + ((size_t)(ct * 2 + 1) * c.L + i) * c.n;
+  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x)
+    sm[padi(j)] = __ldg(&src[galois_pos(j, gal, c.logn)]);
+  __syncthreads();
+  ntt_inv_smem(sm, c.logn, c.mq[i]);
+  uint32_t* dst = digits + ((size_t)ct * c.L + i) * c.n;
+  for (uint32_t kk = threadIdx.x; kk < c.n; kk += blockDim.x) dst[kk] = sm[padi(kk)];
+}
+
+// out[ct][0][l] = acc0 + tau(acc0) + sum_i NTT_l(d_i) * k0[i][l]
+// out[ct][1][l] = acc1 +             sum_i NTT_l(d_i) * k1[i][l]
+// gkj: [L digits][L limbs][4][n] = (k0, k0 Shoup, k1, k1 Shoup), NTT domain.
+__global__ void __launch_bounds__(512) k_ks_apply(DevCtx c, const uint32_t* __restrict__ acc,
+                                                  const uint32_t* __restrict__ digits,
+                                                  const uint32_t* __restrict__ gkj,
+                                                  uint32_t* __restrict__ out, uint32_t gal) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* buf = sm;
+  uint32_t* a0 = sm + padded_words(c.n);
+  uint32_t* a1 = a0 + c.n;
+  const uint32_t ct = blockIdx.x, l = blockIdx.y;
+  const ModP m = c.mq[l];
+  const uint32_t p = m.p, two_p = 2 * p;
+  const uint32_t* c0 = acc + ((size_t)(ct * 2 + 0) * c.L + l) * c.n;
+  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
+    a0[j] = __ldg(&c0[galois_pos(j, gal, c.logn)]);
+    a1[j] = 0;
+  }
+  for (uint32_t i = 0; i < c.L; i++) {
+    const uint32_t* dg = digits + ((size_t)ct * c.L + i) * c.n;
+    for (uint32_t kk = threadIdx.x; kk < c.n; kk += blockDim.x)
+      buf[padi(kk)] = csub(__ldg(&dg[kk]), p);  // d < q_i < 2 q_l
+    __syncthreads();
+    ntt_fwd_smem(buf, c.logn, m);
+    const uint32_t* k = gkj + ((size_t)i * c.L + l) * 4 * c.n;
+    for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
+      const uint32_t x = buf[padi(j)];
+      uint32_t t0 = a0[j] + mulshoup(x, __ldg(&k[j]), __ldg(&k[c.n + j]), p);
+      uint32_t t1 = a1[j] + mulshoup(x, __ldg(&k[2 * c.n + j]), __ldg(&k[3 * c.n + j]), p);
+      a0[j] = csub(t0, two_p);  // a0, a1 kept in [0, 2p)
+      a1[j] = csub(t1, two_p);
+    }
+    __syncthreads();
+  }
+  const uint32_t* c1 = acc + ((size_t)(ct * 2 + 1) * c.L + l) * c.n;
+  uint32_t* o0 = out + ((size_t)(ct * 2 + 0) * c.L + l) * c.n;
+  uint32_t* o1 = out + ((size_t)(ct * 2 + 1) * c.L + l) * c.n;
+  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
+    o0[j] = addm(__ldg(&c0[j]), csub(a0[j], p), p);
+    o1[j] = addm(__ldg(&c1[j]), csub(a1[j], p), p);
+  }
+}
+
+// ------------------------------------------------------------------ export
+// out[ct][poly][l] = INTT_l(acc[ct][poly][l])
+__global__ void __launch_bounds__(512) k_export(DevCtx c, const uint32_t* __restrict__ acc,
+                                                uint32_t* __restrict__ out) {
+  extern __shared__ uint32_t sm[];
+  const uint32_t item = blockIdx.x;  // (ct*2 + poly)*L + l
+  const uint32_t l = item % c.L;
+  const uint32_t* src = acc + (size_t)item * c.n;
+  for (uint32_t kk = threadIdx.x * 4; kk < c.n; kk += blockDim.x * 4) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + kk));
+    sm[padi(kk)] = v.x; sm[padi(kk + 1)] = v.y; sm[padi(kk + 2)] = v.z; sm[padi(kk + 3)] = v.w;
+  }
+  __syncthreads();
+  ntt_inv_smem(sm, c.logn, c.mq[l]);
+  uint32_t* dst = out + (size_t)item * c.n;
+  for (uint32_t kk = threadIdx.x * 4; kk < c.n; kk += blockDim.x * 4)
+    *reinterpret_cast<uint4*>(dst + kk) =
+        make_uint4(sm[padi(kk)], sm[padi(kk + 1)], sm[padi(kk + 2)], sm[padi(kk + 3)]);
+}
+
+inline unsigned ntt_threads(const DevCtx& c) {
+  unsigned t = c.n / 32;
+  return t < 64 ? 64 : (t > 512 ? 512 : t);
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+namespace ephdc {
+
+cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_t* pt,
+                                cudaStream_t st) {
+  const int G = (B + c.cap - 1) / c.cap;
+  const size_t smem = 2 * padded_words(c.n) * sizeof(uint32_t);
+  cudaError_t e = set_smem(k_encode_plain, smem);
+  if (e != cudaSuccess) return e;
+  k_encode_plain<<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                       uint32_t* partial, int splits_max, uint32_t* acc, cudaStream_t st) {
+  constexpr int OC = 4;
+  const int O = 2 * c.Kp;
+  // same rule as the scratch sizing: enough (limb, quad, split) threads to fill
+  // every SM a few times over
+  long per_split = (long)c.L * (c.n / 4) * G;
+  long s = (152L * 2048 + per_split - 1) / per_split;
+  if (s > (long)c.P) s = c.P;
+  if (s > 64) s = 64;
+  if (s < 1) s = 1;
+  (void)splits_max;
+  const int splits = (int)s;
+  const unsigned threads = 256;
+  const unsigned blocks = (c.L * (c.n / 4) + threads - 1) / threads;
+  for (int o0 = 0; o0 < O; o0 += OC) {
+    const int nout = O - o0 < OC ? O - o0 : OC;
+    k_mac<OC><<<dim3(blocks, G, splits), threads, 0, st>>>(c, pt, model, partial, G, splits, o0,
+                                                           nout);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t words = (size_t)G * O * c.L * c.n;
+  k_mac_reduce<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(c, partial, splits, words, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
+                              int count, const uint32_t* gk, cudaStream_t st) {
+  const size_t smem1 = padded_words(c.n) * sizeof(uint32_t);
+  const size_t smem2 = (padded_words(c.n) + 2 * c.n) * sizeof(uint32_t);
+  cudaError_t e = set_smem(k_ks_digits, smem1);
+  if (e == cudaSuccess) e = set_smem(k_ks_apply, smem2);
+  if (e != cudaSuccess) return e;
+  uint32_t* cur = acc;
+  uint32_t* nxt = tmp;
+  const size_t gk_step = (size_t)c.L * c.L * 4 * c.n;
+  uint32_t gal[32];
+  // the Galois elements are recomputed here (3^(W 2^j) mod 2n) to avoid a device read
+  for (uint32_t j = 0; j < c.logr; j++) {
+    uint64_t r = 1, b = 3, ex = (uint64_t)c.W << j, mod = 2ull * c.n;
+    while (ex) {
+      if (ex & 1) r = r * b % mod;
+      b = b * b % mod;
+      ex >>= 1;
+    }
+    gal[j] = (uint32_t)r;
+  }
+  for (uint32_t j = 0; j < c.logr; j++) {
+    k_ks_digits<<<dim3(count, c.L), ntt_threads(c), smem1, st>>>(c, cur, digits, gal[j]);
+    k_ks_apply<<<dim3(count, c.L), ntt_threads(c), smem2, st>>>(c, cur, digits, gk + j * gk_step,
+                                                                nxt, gal[j]);
+    uint32_t* t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export(const DevCtx& c, const uint32_t* acc, int count, uint32_t* out,
+                          cudaStream_t st) {
+  const size_t smem = padded_words(c.n) * sizeof(uint32_t);
+  cudaError_t e = set_smem(k_export, smem);
+  if (e != cudaSuccess) return e;
+  k_export<<<count * 2 * c.L, ntt_threads(c), smem, st>>>(c, acc, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ephdc

@@ -1,0 +1,209 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle, bit for bit.
+
+All comparisons are exact (integer work): secret key, Galois keys, encrypted model
+and every output ciphertext in the coefficient domain, quantised hypervectors,
+plaintext polynomials, and decrypted scores, which must also equal the clear
+integer dot products mod t.  Calls go through the C ABI (via the ctypes binding).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2511_00737_gb300 import ephdc as E
+from paper_2511_00737_gb300 import workload as WL
+
+pytestmark = pytest.mark.gpu
+
+T = 65537
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def _lifted(m, q):
+    """centred lift of plaintext coefficients (mod t) into each limb, [..][L][n]"""
+    mm = m.astype(np.int64)
+    v = np.where(mm <= (T - 1) // 2, mm, mm - T)
+    return np.stack([np.mod(v, p) for p in q], axis=-2).astype(np.uint32)
+
+
+class Case:
+    """One configuration run on both sides from the same seeded inputs."""
+
+    def __init__(self, w, B=None, seed=None):
+        self.w = w
+        self.B = B if B is not None else w.B
+        self.seed = seed if seed is not None else w.seed
+        self.o = O.Oracle(w.n, w.L, w.k, w.k_in, w.r, w.D)
+        self.ctx = E.Context(w.n, w.L, w.k, w.k_in, w.r, w.D, w.F, w.bits, w.shift,
+                             max(self.B, 1))
+        self.X = WL.features(self.seed, self.B, w.F)
+        self.Wt = WL.projection(self.seed, w.D, w.F)
+        self.cls = WL.classes(self.seed, w.k, w.D)
+
+    def oracle_all(self):
+        o = self.o
+        self.s, self.gk = o.keygen(self.seed)
+        self.model = o.encrypt_model(self.seed, self.cls, self.s)
+        self.H, self.m, self.out = o.infer(self.X, self.Wt, self.model, self.gk, self.w.shift,
+                                           self.w.bits)
+        return self
+
+    def gpu_all(self):
+        c = self.ctx
+        self.g_sk, self.g_gk = c.keygen(self.seed)
+        self.g_model = c.encrypt_model(_dev(self.cls), self.g_sk, self.seed)
+        self.g_X, self.g_Wt = _dev(self.X), _dev(self.Wt)
+        self.g_H = c.hdc_encode(self.g_X, self.g_Wt)
+        self.g_pt = c.encode_plain(self.g_H)
+        self.g_out = c.ptct_similarity(self.g_pt, self.B, self.g_model, self.g_gk)
+        torch.cuda.synchronize()
+        return self
+
+
+@pytest.fixture(scope="module")
+def small():
+    return Case(WL.config("small")).oracle_all().gpu_all()
+
+
+# ---------------------------------------------------------------- transforms
+@pytest.mark.parametrize("n,L", [(1024, 2), (4096, 3), (8192, 4), (16384, 6)])
+def test_ntt_natural_order_matches_oracle(n, L):
+    ctx = E.Context(n, L, 2, 1, 1, 64, 16, 8, 0, 4)
+    rng = np.random.default_rng(n)
+    for limb in range(L + 1):
+        p = ctx.q[limb] if limb < L else T
+        psi = O.root_2n(p, n)
+        a = rng.integers(0, p, size=(3, n)).astype(np.uint32)
+        ga = _dev(a.view(np.int32))
+        ctx.ntt_natural(ga, limb)
+        got = _u32(ga)
+        for r in range(3):
+            assert np.array_equal(got[r], O.ntt(a[r], p, psi))
+        ctx.ntt_natural(ga, limb, inverse=True)
+        assert np.array_equal(_u32(ga), a)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- server side
+def test_secret_and_galois_keys_match_oracle(small):
+    c = small
+    assert np.array_equal(c.ctx.sk_to_host(c.g_sk), c.s)
+    assert np.array_equal(c.ctx.gk_to_host_coeff(c.g_gk), c.gk)
+
+
+def test_encrypted_model_matches_oracle(small):
+    c = small
+    got = c.ctx.ct_to_host_coeff(c.g_model, c.o.P * c.o.Kp)
+    assert np.array_equal(got.reshape(c.model.shape), c.model)
+
+
+# ---------------------------------------------------------------- client path
+def test_hdc_encode_matches_oracle(small):
+    assert np.array_equal(small.g_H.cpu().numpy(), small.H)
+
+
+@pytest.mark.parametrize("B,D,F,bits,shift", [(1, 257, 16, 8, 0), (300, 1000, 96, 4, 6),
+                                              (129, 130, 608, 8, 5), (2000, 64, 1024, 2, 9)])
+def test_hdc_encode_ragged_shapes(B, D, F, bits, shift):
+    ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
+    X = WL.features(B + D, B, F)
+    Wt = WL.projection(B + D, D, F)
+    X[0] = 127
+    H = ctx.hdc_encode(_dev(X), _dev(Wt))
+    assert np.array_equal(H.cpu().numpy(), O.hdc_encode(X, Wt, shift, bits))
+    ctx.close()
+
+
+def test_plaintexts_match_oracle(small):
+    c = small
+    G = c.o.groups(c.B)
+    got = c.ctx.plain_to_host_coeff(c.g_pt, G * c.o.P)
+    assert np.array_equal(got, _lifted(c.m.reshape(G * c.o.P, c.o.n), c.o.q))
+
+
+def test_score_ciphertexts_match_oracle(small):
+    c = small
+    got = _u32(c.g_out).reshape(c.out.shape)
+    assert np.array_equal(got, c.out)
+
+
+def test_decrypted_scores_equal_clear_dot_products(small):
+    c = small
+    scores = c.ctx.decrypt_scores(c.g_sk, c.g_out, c.B)
+    clear = O.clear_scores(c.H, c.cls)
+    assert np.array_equal(_u32(scores), clear)
+    assert np.array_equal(c.o.decrypt_scores(c.s, c.out, c.B), clear)
+
+
+def test_fused_infer_equals_step_calls(small):
+    c = small
+    out = c.ctx.infer(c.g_X, c.g_Wt, c.g_model, c.g_gk)
+    assert torch.equal(out, c.g_out)
+
+
+# ---------------------------------------------------------------- layouts and tails
+LAYOUTS = [
+    # n, L, k, k_in, r, D, F, bits, B
+    (1024, 2, 2, 2, 1, 50, 32, 8, 700),     # paper layout, r = 1, no rotation, 2 groups
+    (1024, 3, 3, 1, 4, 41, 16, 4, 600),     # one class per ct, ragged D (41 = 10*4 + 1)
+    (2048, 2, 7, 7, 2, 33, 64, 8, 300),     # 7 packed classes, cap_row = floor(512/7)
+    (4096, 3, 2, 1, 16, 300, 48, 6, 1000),  # 4 rotations, G = 4 with a partial tail
+    (1024, 4, 5, 5, 8, 100, 32, 8, 17),     # 3 rotations, cap_row = 12, B < cap
+]
+
+
+@pytest.mark.parametrize("n,L,k,k_in,r,D,F,bits,B", LAYOUTS)
+def test_layouts_end_to_end(n, L, k, k_in, r, D, F, bits, B):
+    w = WL.Workload(name="t", n=n, L=L, k=k, k_in=k_in, r=r, D=D, F=F, bits=bits, B=B,
+                    seed=1000 + n + r)
+    c = Case(w).oracle_all().gpu_all()
+    assert np.array_equal(c.g_H.cpu().numpy(), c.H)
+    assert np.array_equal(_u32(c.g_out).reshape(c.out.shape), c.out)
+    got = c.ctx.ct_to_host_coeff(c.g_model, c.o.P * c.o.Kp)
+    assert np.array_equal(got.reshape(c.model.shape), c.model)
+    scores = _u32(c.ctx.decrypt_scores(c.g_sk, c.g_out, B))
+    assert np.array_equal(scores, O.clear_scores(c.H, c.cls))
+    c.ctx.close()
+
+
+def test_batch_of_one_and_partial_group():
+    w = WL.config("small")
+    for B in (1, 9):
+        c = Case(w, B=B).oracle_all().gpu_all()
+        assert np.array_equal(_u32(c.g_out).reshape(c.out.shape), c.out)
+        c.ctx.close()
+
+
+# ---------------------------------------------------------------- errors
+def test_errors_are_reported_not_faulted(small):
+    c = small
+    with pytest.raises(E.EphdcError, match="EPHDC_ENOMEM"):
+        E.hdc_encode(c.ctx.ctx, c.g_X, c.g_Wt, c.B + 1000, c.g_H)
+    bad = torch.empty(c.g_H.numel() + 16, dtype=torch.int8, device="cuda")[1:]
+    with pytest.raises(E.EphdcError, match="EPHDC_EINVAL"):
+        E.hdc_encode(c.ctx.ctx, c.g_X, c.g_Wt, c.B, bad)
+    with pytest.raises(E.EphdcError, match="EPHDC_EINVAL"):
+        E.Context(1000, 2, 2, 1, 1, 10, 16, 8, 0, 4)
+
+
+# ---------------------------------------------------------------- full size
+@pytest.mark.slow
+def test_face1024_full_size_bit_exact():
+    """1024 queries, F=608, D=10000, 8-bit HVs, 2 classes, n=8192, 4 primes: every score
+    ciphertext bit-exact, scores equal to the clear dot products mod t."""
+    c = Case(WL.config("face1024")).oracle_all().gpu_all()
+    assert np.array_equal(c.g_H.cpu().numpy(), c.H)
+    assert np.array_equal(_u32(c.g_out).reshape(c.out.shape), c.out)
+    scores = _u32(c.ctx.decrypt_scores(c.g_sk, c.g_out, c.B))
+    assert np.array_equal(scores, O.clear_scores(c.H, c.cls))
+    # the fused call agrees with the step calls
+    out = c.ctx.infer(c.g_X, c.g_Wt, c.g_model, c.g_gk)
+    assert torch.equal(out, c.g_out)
+    c.ctx.close()
