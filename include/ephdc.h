@@ -138,6 +138,33 @@ ephdc_status bfv_ptct_similarity(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t
                                  const void* model_dev, const void* gk_dev, uint32_t* out_ct_dev,
                                  void* stream);
 
+/* Same result as bfv_ptct_similarity, bit for bit, for callers that must not
+ * allocate device memory while they serve: a serving loop whose admission control
+ * has already budgeted every byte of HBM, a process whose memory pool owns the
+ * device, or a latency-critical loop that cannot afford the device-wide
+ * synchronisation a cudaMalloc/cudaFree can cause.  The paper has no counterpart;
+ * it is an interface of this library only.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  Its
+ *    scratch is one array of EPHDC_STATIC_SCRATCH_BYTES (8 MiB) compiled into the
+ *    library as a __device__ variable, which every GPU that loads the library holds
+ *    until the process exits.  The context must still be created beforehand (that
+ *    call allocates the context's tables).
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - All calls share the one array, and it keeps the last call's contents (nothing
+ *    in it needs to start at zero).  Calls whose work overlaps on the GPU -- on
+ *    different streams, or from different contexts on the same device -- race on
+ *    it: serialise them.
+ *  - A batch whose score accumulators need more than the array (2*G*(k/k_in) ciphertexts
+ *    plus one split of partial sums, G = ceil(B / cap)) is rejected with
+ *    EPHDC_EINVAL before anything is enqueued.  With n = 8192 and L = 4 that is
+ *    up to 9 score ciphertexts (G * k/k_in <= 9).
+ * Arguments as for bfv_ptct_similarity. */
+#define EPHDC_STATIC_SCRATCH_BYTES (8u << 20)
+ephdc_status bfv_ptct_similarity_noalloc(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t B,
+                                         const void* model_dev, const void* gk_dev,
+                                         uint32_t* out_ct_dev, void* stream);
+
 /* The whole client path in one call: hdc_encode, bfv_encode_plain and
  * bfv_ptct_similarity on context scratch. */
 ephdc_status ephdc_infer(ephdc_ctx* ctx, const int8_t* X_dev, const int8_t* Wt_dev, int32_t B,

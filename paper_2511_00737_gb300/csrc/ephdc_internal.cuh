@@ -277,4 +277,9 @@ cudaError_t launch_to_coeff(const DevCtx& c, const uint32_t* in, uint32_t* out, 
                             int limb0_is_digit_major, cudaStream_t st);
 cudaError_t launch_sk_to_coeff(const DevCtx& c, const uint32_t* sk, int32_t* out, uint32_t* tmp,
                                cudaStream_t st);
+// context accessors for entry points defined outside host.cu
+const DevCtx* ctx_dev(const ephdc_ctx* c);
+int ctx_device(const ephdc_ctx* c);
+ephdc_status ctx_fail(ephdc_ctx* c, ephdc_status s, const char* msg);
+void ctx_clear_error(ephdc_ctx* c);
 }  // namespace ephdc

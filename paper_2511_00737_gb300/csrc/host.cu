@@ -678,3 +678,10 @@ ephdc_status ephdc_profile_read(ephdc_ctx* c, double* ms, uint64_t* calls, uint6
 }
 
 }  // extern "C"
+
+namespace ephdc {
+const DevCtx* ctx_dev(const ephdc_ctx* c) { return &c->dc; }
+int ctx_device(const ephdc_ctx* c) { return c->device; }
+ephdc_status ctx_fail(ephdc_ctx* c, ephdc_status s, const char* msg) { return fail(c, s, "%s", msg); }
+void ctx_clear_error(ephdc_ctx* c) { c->err.clear(); }
+}  // namespace ephdc

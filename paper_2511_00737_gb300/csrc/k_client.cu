@@ -252,8 +252,8 @@ cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_
   long s = (152L * 2048 + per_split - 1) / per_split;
   if (s > (long)c.P) s = c.P;
   if (s > 64) s = 64;
+  if (s > splits_max) s = splits_max;
   if (s < 1) s = 1;
-  (void)splits_max;
   const int splits = (int)s;
   const unsigned threads = 256;
   const unsigned blocks = (c.L * (c.n / 4) + threads - 1) / threads;

@@ -58,6 +58,8 @@ _SIGS = {
     "ephdc_plain_to_host_coeff": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP]),
     "ephdc_ntt_natural": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP, ctypes.c_int32, ctypes.c_int,
                                          _VP]),
+    "bfv_ptct_similarity_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP,
+                                                    _VP]),
     "ephdc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ephdc_profile_read": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
 }
@@ -158,6 +160,14 @@ def bfv_ptct_similarity(ctx, pt, B, model, gk, out_ct, stream=None):
     _check(ctx, lib().bfv_ptct_similarity(ctx, _ptr(pt, "pt"), B, _ptr(model, "model"),
                                           _ptr(gk, "gk"), _ptr(out_ct, "out_ct"),
                                           _stream(stream)))
+
+
+def bfv_ptct_similarity_noalloc(ctx, pt, B, model, gk, out_ct, stream=None):
+    """bfv_ptct_similarity with its scratch in the library's fixed device array: for
+    callers that must not allocate device memory while serving."""
+    _check(ctx, lib().bfv_ptct_similarity_noalloc(ctx, _ptr(pt, "pt"), B, _ptr(model, "model"),
+                                                  _ptr(gk, "gk"), _ptr(out_ct, "out_ct"),
+                                                  _stream(stream)))
 
 
 def ephdc_infer(ctx, X, Wt, B, model, gk, out_ct, stream=None):
