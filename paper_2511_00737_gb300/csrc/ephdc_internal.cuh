@@ -23,6 +23,11 @@ struct ModP {
   uint64_t mu;             // floor(2^64 / p) for Barrett reduction of 64-bit sums
   const uint2* tw;         // tw[k]  = (psi^brv(k),  Shoup quotient), k in [1, n)
   const uint2* itw;        // itw[k] = (psi^-brv(k), Shoup quotient)
+  // the same twiddles for the contiguous pass (the last 5 forward stages, the first 5
+  // inverse stages) transposed so that a warp's loads are coalesced:
+  // twl[(2^r - 1 + u) * (n/32) + blk] = tw[(n/32 + blk) * 2^r + u], r < 5, u < 2^r
+  const uint2* twl;
+  const uint2* itwl;
 };
 
 // Parameters and tables as seen by kernels (passed by value).
@@ -39,6 +44,7 @@ struct DevCtx {
   const uint32_t* pos2slot;  // device NTT position j -> slot index rho*(n/2) + col
   const uint32_t* slot2pos;  // slot index -> device NTT position
   const uint32_t* galois;    // galois[j] = 3^(W*2^j) mod 2n, j < logr
+  const uint32_t* scatter;   // [(qidx * r + ch) * k_in + jin] -> device position
   uint64_t cdt[EPHDC_CDT_LEN];
 };
 
@@ -218,6 +224,184 @@ static __device__ __noinline__ void ntt_inv_smem(uint32_t* s, uint32_t logn, con
   }
   __syncthreads();
 }
+
+// ------------------------------------------------------------------ NTT, compile-time size
+// The same networks with log2(n) known at compile time: every stride, pass boundary
+// and shared-memory offset is a constant, each element costs one shared load and one
+// shared store per pass, and the final reduction (forward) or n^-1 scaling (inverse)
+// is folded into the last pass.
+template <int LOGN>
+struct NttPlan {
+  static constexpr int LAST = LOGN < 5 ? LOGN : 5;
+  static constexpr int REST = LOGN - LAST;
+  static constexpr int FRONT = (REST + 4) / 5;
+  static constexpr int NP = FRONT + 1;
+  __host__ __device__ static constexpr int K(int i) {
+    return i == FRONT ? LAST : (REST / FRONT + (i < REST % FRONT ? 1 : 0));
+  }
+  __host__ __device__ static constexpr int LOGM0(int i) {
+    int s = 0;
+    for (int j = 0; j < i; j++) s += K(j);
+    return s;
+  }
+};
+
+// Shared-memory element access (padded layout); the first pass of a transform may
+// take a custom loader and the last pass a custom storer, so that the producer
+// (slot gather, lift) and the consumer (global store) fuse into the passes.
+struct SmemLd {
+  const uint32_t* s;
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return s[padi(i)]; }
+};
+struct SmemSt {
+  uint32_t* s;
+  __device__ __forceinline__ void operator()(uint32_t i, uint32_t v) const { s[padi(i)] = v; }
+};
+
+// FINAL: forward -> reduce outputs to [0, p); inverse -> multiply by n^-1, reduce
+template <int LOGN, int K, int LOGM0, bool FWD, bool FINAL, class LD, class ST>
+__device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP& m, LD ld, ST st) {
+  constexpr int LOGS = LOGN - LOGM0 - K;
+  constexpr uint32_t S = 1u << LOGS;
+  static_assert(S == 1 || S >= 32, "pass stride must be contiguous or >= 32");
+  constexpr uint32_t GROUPS = 1u << (LOGN - K);
+  constexpr uint32_t M0 = 1u << LOGM0;
+  // the contiguous pass of a full-size transform reads the transposed twiddle copy
+  constexpr bool CONTIG = S == 1 && K == 5;
+  const uint32_t p = m.p, two_p = 2 * p;
+  for (uint32_t gi = threadIdx.x; gi < GROUPS; gi += blockDim.x) {
+    const uint32_t blk = gi >> LOGS, j0 = gi & (S - 1);
+    const uint32_t base = (blk << (LOGS + K)) + j0;
+    uint32_t x[1 << K];
+#pragma unroll
+    for (int e = 0; e < (1 << K); e++) x[e] = ld(base + e * S);
+    if (FWD) {
+#pragma unroll
+      for (int r = 0; r < K; r++) {
+        const int half = 1 << (K - 1 - r);
+        uint2 w[1 << (K - 1)];
+#pragma unroll
+        for (int u = 0; u < (1 << r); u++)
+          w[u] = CONTIG ? __ldg(&m.twl[((1u << r) - 1 + u) * M0 + blk])
+                        : __ldg(&tw[((M0 + blk) << r) + u]);
+#pragma unroll
+        for (int e = 0; e < (1 << K); e++) {
+          if (e & half) continue;
+          const uint2 ww = w[e >> (K - r)];
+          const uint32_t X = min(x[e], x[e] - two_p);
+          const uint32_t T = mulshoup(x[e + half], ww.x, ww.y, p);
+          x[e] = X + T;
+          x[e + half] = X - T + two_p;
+        }
+      }
+      if (FINAL) {
+#pragma unroll
+        for (int e = 0; e < (1 << K); e++) {
+          const uint32_t v = min(x[e], x[e] - two_p);
+          x[e] = min(v, v - p);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int r = K - 1; r >= 0; r--) {
+        const int half = 1 << (K - 1 - r);
+        uint2 w[1 << (K - 1)];
+#pragma unroll
+        for (int u = 0; u < (1 << r); u++)
+          w[u] = CONTIG ? __ldg(&m.itwl[((1u << r) - 1 + u) * M0 + blk])
+                        : __ldg(&tw[((M0 + blk) << r) + u]);
+#pragma unroll
+        for (int e = 0; e < (1 << K); e++) {
+          if (e & half) continue;
+          const uint2 ww = w[e >> (K - r)];
+          const uint32_t X = x[e], Y = x[e + half];
+          const uint32_t U = X + Y;
+          x[e] = min(U, U - two_p);
+          x[e + half] = mulshoup(X - Y + two_p, ww.x, ww.y, p);
+        }
+      }
+      if (FINAL) {
+#pragma unroll
+        for (int e = 0; e < (1 << K); e++) {
+          const uint32_t v = mulshoup(x[e], m.ninv, m.ninv_sh, p);
+          x[e] = min(v, v - p);
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < (1 << K); e++) st(base + e * S, x[e]);
+  }
+}
+
+template <int LOGN, int I, class LD, class ST>
+__device__ __forceinline__ void fwd_passes(uint32_t* s, const ModP& m, LD ld, ST st) {
+  using Pl = NttPlan<LOGN>;
+  if constexpr (I < Pl::NP) {
+    constexpr bool first = I == 0, last = I == Pl::NP - 1;
+    if constexpr (first && last) {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), true, true>(m.tw, m, ld, st);
+    } else if constexpr (first) {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), true, false>(m.tw, m, ld, SmemSt{s});
+    } else if constexpr (last) {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), true, true>(m.tw, m, SmemLd{s}, st);
+    } else {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), true, false>(m.tw, m, SmemLd{s}, SmemSt{s});
+    }
+    __syncthreads();
+    fwd_passes<LOGN, I + 1>(s, m, ld, st);
+  }
+}
+template <int LOGN, int I, class LD, class ST>
+__device__ __forceinline__ void inv_passes(uint32_t* s, const ModP& m, LD ld, ST st) {
+  using Pl = NttPlan<LOGN>;
+  if constexpr (I >= 0) {
+    constexpr bool first = I == Pl::NP - 1, last = I == 0;
+    if constexpr (first && last) {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true>(m.itw, m, ld, st);
+    } else if constexpr (first) {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, ld, SmemSt{s});
+    } else if constexpr (last) {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true>(m.itw, m, SmemLd{s}, st);
+    } else {
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, SmemLd{s}, SmemSt{s});
+    }
+    __syncthreads();
+    inv_passes<LOGN, I - 1>(s, m, ld, st);
+  }
+}
+// Forward NTT: `ld(i)` supplies natural-order input i (values in [0, 4p)) to the first
+// pass, `st(j, v)` receives device-order output j (in [0, p)) from the last pass;
+// shared buffer `s` (padded) carries the passes in between.  Ends with a barrier.
+template <int LOGN, class LD, class ST>
+__device__ __forceinline__ void ntt_fwd_io(uint32_t* s, const ModP& m, LD ld, ST st) {
+  fwd_passes<LOGN, 0>(s, m, ld, st);
+}
+// Inverse NTT: device-order input (values in [0, 2p)) in, natural-order output in
+// [0, p) out.  Ends with a barrier.
+template <int LOGN, class LD, class ST>
+__device__ __forceinline__ void ntt_inv_io(uint32_t* s, const ModP& m, LD ld, ST st) {
+  inv_passes<LOGN, NttPlan<LOGN>::NP - 1>(s, m, ld, st);
+}
+// in-place variants on the padded shared buffer
+template <int LOGN>
+__device__ __forceinline__ void ntt_fwd_t(uint32_t* s, const ModP& m) {
+  ntt_fwd_io<LOGN>(s, m, SmemLd{s}, SmemSt{s});
+}
+template <int LOGN>
+__device__ __forceinline__ void ntt_inv_t(uint32_t* s, const ModP& m) {
+  ntt_inv_io<LOGN>(s, m, SmemLd{s}, SmemSt{s});
+}
+
+// dispatch a kernel template on log2(n) (n = 1024 .. 16384)
+#define EPHDC_DISPATCH_LOGN(logn, LOGN_, ...)            \
+  switch (logn) {                                        \
+    case 10: { constexpr int LOGN_ = 10; __VA_ARGS__; } break; \
+    case 11: { constexpr int LOGN_ = 11; __VA_ARGS__; } break; \
+    case 12: { constexpr int LOGN_ = 12; __VA_ARGS__; } break; \
+    case 13: { constexpr int LOGN_ = 13; __VA_ARGS__; } break; \
+    case 14: { constexpr int LOGN_ = 14; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;               \
+  }
 
 // ------------------------------------------------------------------ ChaCha20 (RFC 8439)
 __device__ __forceinline__ uint32_t rotl(uint32_t v, int c) { return (v << c) | (v >> (32 - c)); }

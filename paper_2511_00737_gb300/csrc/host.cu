@@ -237,8 +237,8 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
 
   // tables: twiddles for L primes + t (2 x n uint2 each), slot maps, Galois elements
   const int nm = p->L + 1;
-  size_t tw_bytes = (size_t)nm * 2 * n * sizeof(uint2);
-  size_t map_bytes = 2 * (size_t)n * sizeof(uint32_t);
+  size_t tw_bytes = (size_t)nm * 4 * n * sizeof(uint2);  // tw, itw, twl, itwl
+  size_t map_bytes = 3 * (size_t)n * sizeof(uint32_t);  // slot2pos, pos2slot, scatter
   size_t gal_bytes = 64 * sizeof(uint32_t);
   size_t total = align256(tw_bytes) + align256(map_bytes) + align256(gal_bytes);
   std::vector<uint8_t> host(total, 0);
@@ -254,21 +254,33 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   for (int mi = 0; mi < nm; mi++) {
     const uint32_t pm = mi < (int)p->L ? q[mi] : EPHDC_T;
     const uint32_t psi = root2n(pm, n), psi_inv = pw(psi, pm - 2, pm);
-    uint2* f = htw + (size_t)mi * 2 * n;
+    uint2* f = htw + (size_t)mi * 4 * n;
     uint2* b = f + n;
+    uint2* fl = b + n;
+    uint2* bl = fl + n;
     for (uint32_t k = 0; k < n; k++) {
       uint32_t e = brv_host(k, d.logn);
       uint32_t w = pw(psi, e, pm), wi = pw(psi_inv, e, pm);
       f[k] = make_uint2(w, shoup(w, pm));
       b[k] = make_uint2(wi, shoup(wi, pm));
     }
+    // transposed copies for the contiguous 5-stage pass (blocks of 32 elements)
+    const uint32_t M0 = n / 32;
+    for (uint32_t r = 0; r < 5; r++)
+      for (uint32_t u = 0; u < (1u << r); u++)
+        for (uint32_t blk = 0; blk < M0; blk++) {
+          fl[((1u << r) - 1 + u) * M0 + blk] = f[((M0 + blk) << r) + u];
+          bl[((1u << r) - 1 + u) * M0 + blk] = b[((M0 + blk) << r) + u];
+        }
     ModP mp;
     mp.p = pm;
     mp.ninv = pw(n, pm - 2, pm);
     mp.ninv_sh = shoup(mp.ninv, pm);
     mp.mu = (uint64_t)(((unsigned __int128)1 << 64) / pm);
-    mp.tw = dtw + (size_t)mi * 2 * n;
+    mp.tw = dtw + (size_t)mi * 4 * n;
     mp.itw = mp.tw + n;
+    mp.twl = mp.itw + n;
+    mp.itwl = mp.twl + n;
     if (mi < (int)p->L) d.mq[mi] = mp;
     else d.mt = mp;
   }
@@ -285,9 +297,21 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
       s2p[sidx] = pos;
       p2s[pos] = sidx;
     }
+  // scatter[(qidx * r + ch) * k_in + jin] = device position of slot
+  // (rho, ch*W + jin*cap_row + qq), qidx = rho*cap_row + qq: where element ch of the
+  // chunk of query qidx lands for class jin
+  uint32_t* sct = hmap + 2 * n;
+  for (uint32_t qidx = 0; qidx < d.cap; qidx++)
+    for (uint32_t ch = 0; ch < d.r; ch++)
+      for (uint32_t jin = 0; jin < d.k_in; jin++) {
+        const uint32_t rho = qidx / d.cap_row, qq = qidx % d.cap_row;
+        const uint32_t sidx = rho * (n / 2) + ch * d.W + jin * d.cap_row + qq;
+        sct[(qidx * d.r + ch) * d.k_in + jin] = s2p[sidx];
+      }
   for (uint32_t j = 0; j < d.logr; j++) hgal[j] = pw(3, (uint64_t)d.W << j, 2 * n);
   d.slot2pos = (const uint32_t*)((uint8_t*)c->tables + align256(tw_bytes));
   d.pos2slot = d.slot2pos + n;
+  d.scatter = d.slot2pos + 2 * n;
   d.galois = (const uint32_t*)((uint8_t*)c->tables + align256(tw_bytes) + align256(map_bytes));
   cudaError_t ce = cudaMemcpy(c->tables, host.data(), total, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {

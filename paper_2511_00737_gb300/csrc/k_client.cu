@@ -5,7 +5,12 @@
 //                 (HE compute): streams the NTT-domain encrypted model from HBM
 //   rotate_sum    log2(r) Galois rotations with BV key switching, each added back
 //   export        inverse NTT of the score ciphertexts to the coefficient domain
+// The transforms are instantiated per ring degree (log2 n = 10..14).
+#include <cooperative_groups.h>
+
 #include "ephdc_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -18,49 +23,52 @@ __device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t 
 }
 
 // ------------------------------------------------------------------ EncPt
-// One CTA per plaintext (g, i).  Query beta = g*cap + rho*cap_row + qq, dimension
-// d = i*r + ch lands in slot (rho, ch*W + jin*cap_row + qq) for every jin < k_in.
-__global__ void __launch_bounds__(512) k_encode_plain(DevCtx c, const int8_t* __restrict__ H,
+// One CTA per plaintext (g, i).  Query beta = g*cap + qidx (qidx = rho*cap_row + qq)
+// and dimension d = i*r + ch land in slot (rho, ch*W + jin*cap_row + qq) for every
+// jin < k_in.  Threads walk the cap x r block of H row by row (consecutive threads
+// read consecutive bytes of a query row) and scatter each value to its k_in device
+// positions through the context's scatter table; then the inverse NTT mod t gives the
+// plaintext coefficients, and for each limb the centred lift feeds the forward NTT,
+// whose output is staged in shared memory and stored with 16-byte writes.
+template <int LOGN>
+__global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3) k_encode_plain(DevCtx c, const int8_t* __restrict__ H,
                                                       int B, uint32_t* __restrict__ pt) {
+  constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   uint32_t* mb = sm;
-  uint32_t* wb = sm + padded_words(c.n);
+  uint32_t* wb = sm + padded_words(N);
   const uint32_t gi = blockIdx.x;
   const uint32_t g = gi / c.P, i = gi - g * c.P;
-  const uint32_t half = c.n >> 1;
-  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
-    const uint32_t sidx = __ldg(&c.pos2slot[j]);
-    const uint32_t rho = sidx >= half;
-    const uint32_t col = sidx - rho * half;
-    const uint32_t ch = col / c.W, within = col - ch * c.W;
-    const uint32_t jin = within / c.cap_row, qq = within - jin * c.cap_row;
-    uint32_t v = 0;
-    if (jin < c.k_in) {
-      const uint32_t d = i * c.r + ch;
-      const uint64_t beta = (uint64_t)g * c.cap + rho * c.cap_row + qq;
-      if (d < c.D && beta < (uint64_t)B) {
-        const int h = H[beta * c.D + d];
-        v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
-      }
-    }
-    mb[padi(j)] = v;
+  for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) mb[padi(j)] = 0;
+  __syncthreads();
+  const uint32_t qlim = min((uint32_t)c.cap, (uint32_t)(B - (int)(g * c.cap)));
+  const uint32_t d0 = i * c.r;
+  const uint32_t r = c.r, logr = c.logr, kin = c.k_in, D = c.D;
+  const uint32_t dlim = D - d0 < r ? D - d0 : r;
+  const int8_t* Hg = H + (size_t)g * c.cap * D + d0;
+  const uint32_t total = qlim << logr;
+  for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const uint32_t qidx = idx >> logr, ch = idx & (r - 1);
+    if (ch >= dlim) continue;
+    const int h = Hg[(size_t)qidx * D + ch];
+    const uint32_t v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
+    const uint32_t* sc = c.scatter + (size_t)idx * kin;
+    for (uint32_t jin = 0; jin < kin; jin++) mb[padi(__ldg(&sc[jin]))] = v;
   }
   __syncthreads();
-  ntt_inv_smem(mb, c.logn, c.mt);  // slots -> plaintext coefficients in [0, t)
-  const uint32_t thalf = (EPHDC_T - 1) / 2;
+  ntt_inv_t<LOGN>(mb, c.mt);  // slots -> coefficients in [0, t)
+  constexpr uint32_t thalf = (EPHDC_T - 1) / 2;
   for (uint32_t l = 0; l < c.L; l++) {
     const uint32_t p = c.mq[l].p;
-    for (uint32_t kk = threadIdx.x; kk < c.n; kk += blockDim.x) {
-      const uint32_t m = mb[padi(kk)];
-      wb[padi(kk)] = m <= thalf ? m : m + p - EPHDC_T;  // centred lift
-    }
-    __syncthreads();
-    ntt_fwd_smem(wb, c.logn, c.mq[l]);
-    uint32_t* dst = pt + ((size_t)gi * c.L + l) * c.n;
-    for (uint32_t kk = threadIdx.x * 4; kk < c.n; kk += blockDim.x * 4) {
-      uint4 v = make_uint4(wb[padi(kk)], wb[padi(kk + 1)], wb[padi(kk + 2)], wb[padi(kk + 3)]);
-      *reinterpret_cast<uint4*>(dst + kk) = v;
-    }
+    auto lift = [=](uint32_t k) -> uint32_t {
+      const uint32_t v = mb[padi(k)];
+      return v <= thalf ? v : v + p - EPHDC_T;  // centred lift into Z_{q_l}
+    };
+    ntt_fwd_io<LOGN>(wb, c.mq[l], lift, SmemSt{wb});
+    uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
+    for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
+      dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
+                          wb[padi(4 * k + 3)]);
     __syncthreads();
   }
 }
@@ -141,81 +149,96 @@ __global__ void k_mac_reduce(DevCtx c, const uint32_t* __restrict__ partial, int
 // ------------------------------------------------------------------ rotations
 // digits[ct][i][:] = INTT_{q_i}(tau_g(c1 limb i)): the RNS digits of the rotated c1
 // as integer polynomials with coefficients in [0, q_i).
+template <int LOGN>
 __global__ void __launch_bounds__(512) k_ks_digits(DevCtx c, const uint32_t* __restrict__ acc,
                                                    uint32_t* __restrict__ digits, uint32_t gal) {
+  constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   const uint32_t ct = blockIdx.x, i = blockIdx.y;
-  const uint32_t* src = acc + ((size_t)(ct * 2 + 1) * c.L + i) * c.n;
-  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x)
-    sm[padi(j)] = __ldg(&src[galois_pos(j, gal, c.logn)]);
-  __syncthreads();
-  ntt_inv_smem(sm, c.logn, c.mq[i]);
-  uint32_t* dst = digits + ((size_t)ct * c.L + i) * c.n;
-  for (uint32_t kk = threadIdx.x; kk < c.n; kk += blockDim.x) dst[kk] = sm[padi(kk)];
+  const uint32_t* src = acc + ((size_t)(ct * 2 + 1) * c.L + i) * N;
+  uint32_t* dst = digits + ((size_t)ct * c.L + i) * N;
+  ntt_inv_io<LOGN>(sm, c.mq[i], [=](uint32_t j) { return __ldg(&src[galois_pos(j, gal, LOGN)]); },
+                   [=](uint32_t k, uint32_t v) { dst[k] = v; });
 }
 
-// out[ct][0][l] = acc0 + tau(acc0) + sum_i NTT_l(d_i) * k0[i][l]
-// out[ct][1][l] = acc1 +             sum_i NTT_l(d_i) * k1[i][l]
+// Key switch and add, one thread-block cluster of L CTAs per (ciphertext, target limb
+// l); cluster rank i owns RNS digit i:
+//   P0_i = NTT_l(d_i) * k0[i][l],  P1_i = NTT_l(d_i) * k1[i][l]   (in its shared memory)
+// then rank i sums its 1/L slice of the coefficients over the whole cluster through
+// distributed shared memory:
+//   out[ct][0][l] = acc0 + tau(acc0) + sum_i P0_i,   out[ct][1][l] = acc1 + sum_i P1_i.
+// For i = l the digit's transform is tau(acc1 limb l) itself and is read directly.
 // gkj: [L digits][L limbs][4][n] = (k0, k0 Shoup, k1, k1 Shoup), NTT domain.
-__global__ void __launch_bounds__(512) k_ks_apply(DevCtx c, const uint32_t* __restrict__ acc,
-                                                  const uint32_t* __restrict__ digits,
-                                                  const uint32_t* __restrict__ gkj,
-                                                  uint32_t* __restrict__ out, uint32_t gal) {
+template <int LOGN>
+__global__ void __launch_bounds__(512) k_ks_cluster(DevCtx c, const uint32_t* __restrict__ acc,
+                                                    const uint32_t* __restrict__ digits,
+                                                    const uint32_t* __restrict__ gkj,
+                                                    uint32_t* __restrict__ out, uint32_t gal) {
+  constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
-  uint32_t* buf = sm;
-  uint32_t* a0 = sm + padded_words(c.n);
-  uint32_t* a1 = a0 + c.n;
-  const uint32_t ct = blockIdx.x, l = blockIdx.y;
+  uint32_t* p0 = sm;                    // padded, also the transform buffer
+  uint32_t* p1 = sm + padded_words(N);  // padded
+  cg::cluster_group cluster = cg::this_cluster();
+  const uint32_t i = blockIdx.x, l = blockIdx.y, ct = blockIdx.z;
   const ModP m = c.mq[l];
-  const uint32_t p = m.p, two_p = 2 * p;
-  const uint32_t* c0 = acc + ((size_t)(ct * 2 + 0) * c.L + l) * c.n;
-  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
-    a0[j] = __ldg(&c0[galois_pos(j, gal, c.logn)]);
-    a1[j] = 0;
+  const uint32_t p = m.p;
+  const uint32_t* k = gkj + ((size_t)i * c.L + l) * 4 * N;
+  const uint32_t* c1 = acc + ((size_t)(ct * 2 + 1) * c.L + l) * N;
+  if (i == l) {
+    for (uint32_t j = threadIdx.x; j < N; j += blockDim.x)
+      p0[padi(j)] = __ldg(&c1[galois_pos(j, gal, LOGN)]);
+  } else {
+    const uint32_t* dg = digits + ((size_t)ct * c.L + i) * N;
+    ntt_fwd_io<LOGN>(p0, m, [=](uint32_t kk) { return csub(__ldg(&dg[kk]), p); },  // d < 2 q_l
+                     SmemSt{p0});
   }
-  for (uint32_t i = 0; i < c.L; i++) {
-    const uint32_t* dg = digits + ((size_t)ct * c.L + i) * c.n;
-    for (uint32_t kk = threadIdx.x; kk < c.n; kk += blockDim.x)
-      buf[padi(kk)] = csub(__ldg(&dg[kk]), p);  // d < q_i < 2 q_l
-    __syncthreads();
-    ntt_fwd_smem(buf, c.logn, m);
-    const uint32_t* k = gkj + ((size_t)i * c.L + l) * 4 * c.n;
-    for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
-      const uint32_t x = buf[padi(j)];
-      uint32_t t0 = a0[j] + mulshoup(x, __ldg(&k[j]), __ldg(&k[c.n + j]), p);
-      uint32_t t1 = a1[j] + mulshoup(x, __ldg(&k[2 * c.n + j]), __ldg(&k[3 * c.n + j]), p);
-      a0[j] = csub(t0, two_p);  // a0, a1 kept in [0, 2p)
-      a1[j] = csub(t1, two_p);
+  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) {
+    const uint32_t x = p0[padi(j)];
+    p0[padi(j)] = mulshoup(x, __ldg(&k[j]), __ldg(&k[N + j]), p);
+    p1[padi(j)] = mulshoup(x, __ldg(&k[2 * N + j]), __ldg(&k[3 * N + j]), p);
+  }
+  cluster.sync();
+  const uint32_t L = c.L;
+  const uint32_t slice = (N + L - 1) / L;
+  const uint32_t j0 = i * slice, j1 = min(N, j0 + slice);
+  const uint32_t* c0 = acc + ((size_t)(ct * 2 + 0) * c.L + l) * N;
+  uint32_t* o0 = out + ((size_t)(ct * 2 + 0) * c.L + l) * N;
+  uint32_t* o1 = out + ((size_t)(ct * 2 + 1) * c.L + l) * N;
+  for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[galois_pos(j, gal, LOGN)]);
+    uint64_t s1 = __ldg(&c1[j]);
+    for (uint32_t r = 0; r < L; r++) {
+      const uint32_t* q0 = cluster.map_shared_rank(p0, r);
+      const uint32_t* q1 = cluster.map_shared_rank(p1, r);
+      s0 += q0[padi(j)];
+      s1 += q1[padi(j)];
     }
-    __syncthreads();
+    o0[j] = red64(s0, p, m.mu);
+    o1[j] = red64(s1, p, m.mu);
   }
-  const uint32_t* c1 = acc + ((size_t)(ct * 2 + 1) * c.L + l) * c.n;
-  uint32_t* o0 = out + ((size_t)(ct * 2 + 0) * c.L + l) * c.n;
-  uint32_t* o1 = out + ((size_t)(ct * 2 + 1) * c.L + l) * c.n;
-  for (uint32_t j = threadIdx.x; j < c.n; j += blockDim.x) {
-    o0[j] = addm(__ldg(&c0[j]), csub(a0[j], p), p);
-    o1[j] = addm(__ldg(&c1[j]), csub(a1[j], p), p);
-  }
+  cluster.sync();  // keep every CTA's shared memory alive until all slices are read
 }
 
 // ------------------------------------------------------------------ export
 // out[ct][poly][l] = INTT_l(acc[ct][poly][l])
+template <int LOGN>
 __global__ void __launch_bounds__(512) k_export(DevCtx c, const uint32_t* __restrict__ acc,
                                                 uint32_t* __restrict__ out) {
+  constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   const uint32_t item = blockIdx.x;  // (ct*2 + poly)*L + l
   const uint32_t l = item % c.L;
-  const uint32_t* src = acc + (size_t)item * c.n;
-  for (uint32_t kk = threadIdx.x * 4; kk < c.n; kk += blockDim.x * 4) {
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + kk));
-    sm[padi(kk)] = v.x; sm[padi(kk + 1)] = v.y; sm[padi(kk + 2)] = v.z; sm[padi(kk + 3)] = v.w;
+  const uint32_t* src = acc + (size_t)item * N;
+  uint32_t* dst = out + (size_t)item * N;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
+    const uint4 v = __ldg(&s4[k]);
+    sm[padi(4 * k)] = v.x; sm[padi(4 * k + 1)] = v.y; sm[padi(4 * k + 2)] = v.z;
+    sm[padi(4 * k + 3)] = v.w;
   }
   __syncthreads();
-  ntt_inv_smem(sm, c.logn, c.mq[l]);
-  uint32_t* dst = out + (size_t)item * c.n;
-  for (uint32_t kk = threadIdx.x * 4; kk < c.n; kk += blockDim.x * 4)
-    *reinterpret_cast<uint4*>(dst + kk) =
-        make_uint4(sm[padi(kk)], sm[padi(kk + 1)], sm[padi(kk + 2)], sm[padi(kk + 3)]);
+  ntt_inv_io<LOGN>(sm, c.mq[l], SmemLd{sm}, [=](uint32_t k, uint32_t v) { dst[k] = v; });
 }
 
 inline unsigned ntt_threads(const DevCtx& c) {
@@ -236,9 +259,11 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
                                 cudaStream_t st) {
   const int G = (B + c.cap - 1) / c.cap;
   const size_t smem = 2 * padded_words(c.n) * sizeof(uint32_t);
-  cudaError_t e = set_smem(k_encode_plain, smem);
-  if (e != cudaSuccess) return e;
-  k_encode_plain<<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
+  EPHDC_DISPATCH_LOGN(c.logn, LG, {
+    cudaError_t e = set_smem(k_encode_plain<LG>, smem);
+    if (e != cudaSuccess) return e;
+    k_encode_plain<LG><<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
+  });
   return cudaGetLastError();
 }
 
@@ -272,16 +297,12 @@ cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_
 cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
                               int count, const uint32_t* gk, cudaStream_t st) {
   const size_t smem1 = padded_words(c.n) * sizeof(uint32_t);
-  const size_t smem2 = (padded_words(c.n) + 2 * c.n) * sizeof(uint32_t);
-  cudaError_t e = set_smem(k_ks_digits, smem1);
-  if (e == cudaSuccess) e = set_smem(k_ks_apply, smem2);
-  if (e != cudaSuccess) return e;
+  const size_t smem2 = 2 * padded_words(c.n) * sizeof(uint32_t);
   uint32_t* cur = acc;
   uint32_t* nxt = tmp;
   const size_t gk_step = (size_t)c.L * c.L * 4 * c.n;
   uint32_t gal[32];
-  // the Galois elements are recomputed here (3^(W 2^j) mod 2n) to avoid a device read
-  for (uint32_t j = 0; j < c.logr; j++) {
+  for (uint32_t j = 0; j < c.logr; j++) {  // 3^(W 2^j) mod 2n
     uint64_t r = 1, b = 3, ex = (uint64_t)c.W << j, mod = 2ull * c.n;
     while (ex) {
       if (ex & 1) r = r * b % mod;
@@ -290,23 +311,43 @@ cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uin
     }
     gal[j] = (uint32_t)r;
   }
-  for (uint32_t j = 0; j < c.logr; j++) {
-    k_ks_digits<<<dim3(count, c.L), ntt_threads(c), smem1, st>>>(c, cur, digits, gal[j]);
-    k_ks_apply<<<dim3(count, c.L), ntt_threads(c), smem2, st>>>(c, cur, digits, gk + j * gk_step,
-                                                                nxt, gal[j]);
-    uint32_t* t = cur;
-    cur = nxt;
-    nxt = t;
-  }
+  EPHDC_DISPATCH_LOGN(c.logn, LG, {
+    cudaError_t e = set_smem(k_ks_digits<LG>, smem1);
+    if (e == cudaSuccess) e = set_smem(k_ks_cluster<LG>, smem2);
+    if (e != cudaSuccess) return e;
+    for (uint32_t j = 0; j < c.logr; j++) {
+      k_ks_digits<LG><<<dim3(count, c.L), ntt_threads(c), smem1, st>>>(c, cur, digits, gal[j]);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(c.L, c.L, count);
+      cfg.blockDim = dim3(ntt_threads(c));
+      cfg.dynamicSmemBytes = smem2;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = c.L;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = cudaLaunchKernelEx(&cfg, k_ks_cluster<LG>, c, (const uint32_t*)cur,
+                             (const uint32_t*)digits, gk + j * gk_step, nxt, gal[j]);
+      if (e != cudaSuccess) return e;
+      uint32_t* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+  });
   return cudaGetLastError();
 }
 
 cudaError_t launch_export(const DevCtx& c, const uint32_t* acc, int count, uint32_t* out,
                           cudaStream_t st) {
   const size_t smem = padded_words(c.n) * sizeof(uint32_t);
-  cudaError_t e = set_smem(k_export, smem);
-  if (e != cudaSuccess) return e;
-  k_export<<<count * 2 * c.L, ntt_threads(c), smem, st>>>(c, acc, out);
+  EPHDC_DISPATCH_LOGN(c.logn, LG, {
+    cudaError_t e = set_smem(k_export<LG>, smem);
+    if (e != cudaSuccess) return e;
+    k_export<LG><<<count * 2 * c.L, ntt_threads(c), smem, st>>>(c, acc, out);
+  });
   return cudaGetLastError();
 }
 
