@@ -119,7 +119,9 @@ ephdc_status bfv_decrypt_scores(ephdc_ctx* ctx, const void* sk_dev, const uint32
 /* HDC encoding (Sec. 2.1 random projection) with quantisation (Sec. 5.1):
  * A = X * Wt^T exactly in int32, H = clamp(floor((A + 2^(s-1)) / 2^s), -2^(b-1),
  * 2^(b-1)-1).  X_dev: int8 [B][F]; Wt_dev: int8 [D][F] (row d = weights of
- * dimension d); H_dev: int8 [B][D].  1 <= B <= max_batch. */
+ * dimension d); H_dev: int8 [B][D].  1 <= B <= max_batch.  The product runs on the
+ * tensor cores in fp16 x fp16 -> fp32, which is exact here: operands are integers of
+ * magnitude <= 128 and every partial sum stays below 2^24 (F <= 65536). */
 ephdc_status hdc_encode(ephdc_ctx* ctx, const int8_t* X_dev, const int8_t* Wt_dev, int32_t B,
                         int8_t* H_dev, void* stream);
 
@@ -192,6 +194,13 @@ ephdc_status ephdc_plain_to_host_coeff(ephdc_ctx* ctx, const uint32_t* pt_dev, i
  * transform against other implementations. */
 ephdc_status ephdc_ntt_natural(ephdc_ctx* ctx, uint32_t limb, uint32_t* poly_dev, int32_t count,
                                int inverse, void* stream);
+
+/* Pipeline waits inside the kernels (tensor-core producer/consumer barriers) are
+ * bounded: a wait that gives up records a code in the context's device status word,
+ * the kernel skips its remaining work and returns, and the context stays usable.
+ * This call waits for all work on the device and returns EPHDC_ETIMEOUT (clearing
+ * the word) if any wait gave up since the last call, else EPHDC_OK. */
+ephdc_status ephdc_device_status(ephdc_ctx* ctx);
 
 /* ---------------------------------------------------------------- measurement */
 /* Stages of the client path, for per-stage device timing. */

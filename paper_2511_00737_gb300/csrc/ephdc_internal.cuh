@@ -45,6 +45,10 @@ struct DevCtx {
   const uint32_t* slot2pos;  // slot index -> device NTT position
   const uint32_t* galois;    // galois[j] = 3^(W*2^j) mod 2n, j < logr
   const uint32_t* scatter;   // [(qidx * r + ch) * k_in + jin] -> device position
+  // context scratch used by kernels: fp16 copies of the HDC operands, status word
+  uint16_t* xh;              // [max_batch][F] fp16 features
+  uint16_t* wh;              // [D][F] fp16 projection
+  uint32_t* status;          // nonzero when a bounded device wait gave up
   uint64_t cdt[EPHDC_CDT_LEN];
 };
 

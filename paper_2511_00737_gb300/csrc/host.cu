@@ -197,7 +197,8 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   if (p->r < 1 || (p->r & (p->r - 1)) || p->r > n / (2 * p->k_in))
     return fail(nullptr, EPHDC_EINVAL, "r must be a power of two <= n/(2 k_in), got %u", p->r);
   if (p->D < 1) return fail(nullptr, EPHDC_EINVAL, "D must be positive");
-  if (p->F < 16 || p->F % 16) return fail(nullptr, EPHDC_EINVAL, "F must be a positive multiple of 16");
+  if (p->F < 16 || p->F % 16 || p->F > 65536)
+    return fail(nullptr, EPHDC_EINVAL, "F must be a multiple of 16 in [16, 65536]");
   if (p->hv_bits < 2 || p->hv_bits > 8) return fail(nullptr, EPHDC_EINVAL, "hv_bits must be in [2, 8]");
   if (p->shift < 0 || p->shift > 30) return fail(nullptr, EPHDC_EINVAL, "shift must be in [0, 30]");
   if (p->max_batch < 1) return fail(nullptr, EPHDC_EINVAL, "max_batch must be positive");
@@ -374,6 +375,9 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   size_t oacc = off; off += align256(acc_bytes);
   size_t otmp = off; off += align256(acc_bytes);
   size_t odig = off; off += align256((size_t)c->G_max * d.Kp * d.L * poly);
+  size_t oxh = off; off += align256((size_t)p->max_batch * p->F * 2);
+  size_t owh = off; off += align256((size_t)p->D * p->F * 2);
+  size_t ost = off; off += 256;
   c->scratch_bytes = off;
   if (cudaMalloc(&c->scratch, off) != cudaSuccess) {
     cudaGetLastError();
@@ -388,6 +392,15 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   c->acc = (uint32_t*)(sb + oacc);
   c->tmp = (uint32_t*)(sb + otmp);
   c->digits = (uint32_t*)(sb + odig);
+  d.xh = (uint16_t*)(sb + oxh);
+  d.wh = (uint16_t*)(sb + owh);
+  d.status = (uint32_t*)(sb + ost);
+  if (cudaMemset(d.status, 0, 256) != cudaSuccess) {
+    cudaFree(c->scratch);
+    cudaFree(c->tables);
+    delete c;
+    return fail(nullptr, EPHDC_ECUDA, "status word initialisation failed");
+  }
   *out = c;
   return EPHDC_OK;
 }
@@ -669,6 +682,20 @@ ephdc_status ephdc_ntt_natural(ephdc_ctx* c, uint32_t limb, uint32_t* poly, int3
   if (limb > c->dc.L || count < 1) return fail(c, EPHDC_EINVAL, "bad limb or count");
   return launched(c, ephdc::launch_ntt_natural(c->dc, limb, poly, count, inverse,
                                                (cudaStream_t)stream), "ntt_natural");
+}
+
+ephdc_status ephdc_device_status(ephdc_ctx* c) {
+  CHECK_CTX(c);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status(c, e, "device_status");
+  uint32_t word = 0;
+  e = cudaMemcpy(&word, c->dc.status, sizeof word, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(c, e, "device_status");
+  if (word) {
+    cudaMemset(c->dc.status, 0, sizeof word);
+    return fail(c, EPHDC_ETIMEOUT, "a bounded device wait gave up (code %u)", word);
+  }
+  return EPHDC_OK;
 }
 
 ephdc_status ephdc_profile_enable(ephdc_ctx* c, int on) {

@@ -1,0 +1,275 @@
+// HDC encoding (Sec. 2.1 random projection) on the 5th-generation tensor cores,
+// with the quantiser of Sec. 5.1 fused into the epilogue:
+//   H = clamp(floor((X Wt^T + 2^(s-1)) / 2^s), -2^(b-1), 2^(b-1)-1).
+//
+// sm_103a has no tcgen05 integer MMA, and the legacy int8 mma.sync path runs at a
+// quarter of the fp16 rate on this part.  The projection is computed exactly in
+// fp16 x fp16 -> fp32 instead: every int8 feature and +-1 weight is an fp16 value,
+// every product is an integer of magnitude <= 128, and every partial sum is an
+// integer of magnitude <= 128 F < 2^24 (F <= 65536), so no rounding ever happens.
+//
+// Structure (one 128 x 128 output tile per CTA, 4 warps):
+//   - int8 operands are widened to fp16 in global scratch by a streaming kernel;
+//   - warp 0 / lane 0 issues TMA loads (128-byte swizzle) of 64-wide K slices of
+//     both operands into a 3-stage shared-memory ring (mbarrier expect-tx);
+//   - warp 1 / lane 0 issues tcgen05.mma (M=128, N=128, K=16) into a TMEM
+//     accumulator and frees ring stages with tcgen05.commit;
+//   - all 4 warps read their 32 TMEM lanes with tcgen05.ld, quantise and store.
+// Every mbarrier wait is bounded; on timeout the kernel records an error code in a
+// device status word, skips the remaining work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include "ephdc_internal.cuh"
+
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 64, STAGES = 3;
+constexpr uint32_t A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2;
+constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = TN;  // fp32 accumulator: 128 lanes x 128 columns
+
+// instruction descriptor, kind::f16: D = f32 (bits 4-5 = 1), A = B = f16 (bits 7-9,
+// 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: gives up after ~2^31 cycles (about a second) and records `code`
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status,
+                                          uint32_t code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicCAS(status, 0u, code);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%3, %4}], [%2];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B
+// apart (SBO), descriptor version 1 at bit 46, layout SWIZZLE_128B (2) at bit 61
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128) k_hdc_tc(const __grid_constant__ CUtensorMap ta,
+                                                const __grid_constant__ CUtensorMap tb, int B,
+                                                int D, int F, int shift, int bits,
+                                                int8_t* __restrict__ H, uint32_t* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int nk = (F + TK - 1) / TK;
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
+  const uint32_t done = smem_u32(&bars[2 * STAGES]);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads of K slice k into stage k % STAGES
+    for (int k = 0; k < nk; k++) {
+      const int s = k % STAGES;
+      if (k >= STAGES && !mbar_wait(empty(s), ((k / STAGES) - 1) & 1, status, 1)) break;
+      mbar_expect_tx(full(s), STAGE_BYTES);
+      tma_load_2d(smem_u32(sA + s * A_BYTES), &ta, k * TK, m0, full(s));
+      tma_load_2d(smem_u32(sB + s * B_BYTES), &tb, k * TK, n0, full(s));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: 4 MMAs of K = 16 per 64-wide slice
+    for (int k = 0; k < nk; k++) {
+      const int s = k % STAGES;
+      if (!mbar_wait(full(s), (k / STAGES) & 1, status, 2)) break;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; kk++)
+        tc_mma(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), (k | kk) != 0);
+      tc_commit(empty(s));
+    }
+    tc_commit(done);  // arrives when every MMA issued above has completed
+  }
+  __syncwarp();
+  // warp-uniform: the TMEM loads below are .sync.aligned
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, status, 3));
+  tc_fence_after();
+
+  if (ok) {
+    const int row = m0 + 32 * (int)warp + (int)lane;
+    const int rnd = shift > 0 ? 1 << (shift - 1) : 0;
+    const int lo = -(1 << (bits - 1)), hi = (1 << (bits - 1)) - 1;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 32) {
+      uint32_t v[32];
+      tc_ld32(tmem + ((32 * warp) << 16) + c0, v);  // this warp's 32 lanes, 32 columns
+      if (row < B) {
+        int8_t q[32];
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+          int a = __float2int_rz(__uint_as_float(v[e]));  // an exact integer
+          a = (a + rnd) >> shift;                          // floor division by 2^s
+          q[e] = (int8_t)(a < lo ? lo : (a > hi ? hi : a));
+        }
+        const int col = n0 + c0;
+        int8_t* dst = H + (size_t)row * D + col;
+        if (col + 32 <= D && (((uintptr_t)dst) & 15) == 0) {
+          reinterpret_cast<int4*>(dst)[0] = *reinterpret_cast<const int4*>(&q[0]);
+          reinterpret_cast<int4*>(dst)[1] = *reinterpret_cast<const int4*>(&q[16]);
+        } else {
+          for (int e = 0; e < 32 && col + e < D; e++) dst[e] = q[e];
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+}
+
+// int8 -> fp16, 16 elements per thread (n16 chunks of 16)
+__global__ void k_widen(const int8_t* __restrict__ src, __half* __restrict__ dst, size_t n16) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(src) + i);
+    const int8_t* b = reinterpret_cast<const int8_t*>(&v);
+    __align__(16) __half h[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) h[e] = __short2half_rn((short)b[e]);
+    reinterpret_cast<int4*>(dst + 16 * i)[0] = reinterpret_cast<const int4*>(h)[0];
+    reinterpret_cast<int4*>(dst + 16 * i)[1] = reinterpret_cast<const int4*>(h)[1];
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+cudaError_t tensor_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows,
+                       uint32_t box_rows) {
+  if (!g_encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TK, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+namespace ephdc {
+
+cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt, int B,
+                              int8_t* H, cudaStream_t st) {
+  const size_t nx = (size_t)B * c.F / 16, nw = (size_t)c.D * c.F / 16;
+  auto blocks = [](size_t n) { return (unsigned)((n + 255) / 256 < 2432 ? (n + 255) / 256 : 2432); };
+  k_widen<<<blocks(nx), 256, 0, st>>>(X, reinterpret_cast<__half*>(c.xh), nx);
+  k_widen<<<blocks(nw), 256, 0, st>>>(Wt, reinterpret_cast<__half*>(c.wh), nw);
+  CUtensorMap ta, tb;
+  cudaError_t e = tensor_map(&ta, c.xh, c.F, (uint64_t)B, TM);
+  if (e == cudaSuccess) e = tensor_map(&tb, c.wh, c.F, c.D, TN);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_hdc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  dim3 grid((c.D + TN - 1) / TN, (B + TM - 1) / TM);
+  k_hdc_tc<<<grid, 128, SMEM_BYTES, st>>>(ta, tb, B, (int)c.D, (int)c.F, c.shift, (int)c.bits, H,
+                                          c.status);
+  return cudaGetLastError();
+}
+
+}  // namespace ephdc

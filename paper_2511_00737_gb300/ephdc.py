@@ -60,6 +60,7 @@ _SIGS = {
                                          _VP]),
     "bfv_ptct_similarity_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP,
                                                     _VP]),
+    "ephdc_device_status": (ctypes.c_int, [_VP]),
     "ephdc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ephdc_profile_read": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
 }
@@ -288,6 +289,10 @@ class Context:
         _check(self.ctx, lib().ephdc_plain_to_host_coeff(self.ctx, _ptr(pt, "pt"), count,
                                                          host.ctypes.data_as(_VP)))
         return host
+
+    def device_status(self):
+        """Raise EphdcError(EPHDC_ETIMEOUT) if a bounded device wait gave up."""
+        _check(self.ctx, lib().ephdc_device_status(self.ctx))
 
     def profile(self, on=True):
         _check(self.ctx, lib().ephdc_profile_enable(self.ctx, 1 if on else 0))

@@ -121,6 +121,23 @@ def test_hdc_encode_ragged_shapes(B, D, F, bits, shift):
     ctx.close()
 
 
+def test_hdc_encode_extreme_magnitudes_exact():
+    """|X Wt^T| up to 127 * F with F = 1024: the fp16-operand tensor-core product must
+    still be the exact integer (all partial sums < 2^24)."""
+    B, D, F = 256, 384, 1024
+    X = WL.features(5, B, F)
+    Wt = WL.projection(5, D, F)
+    X[:64] = 127
+    Wt[:100] = -1
+    Wt[100:200] = 1
+    for shift, bits in [(0, 8), (10, 8), (14, 4)]:
+        ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
+        H = ctx.hdc_encode(_dev(X), _dev(Wt))
+        assert np.array_equal(H.cpu().numpy(), O.hdc_encode(X, Wt, shift, bits))
+        ctx.device_status()
+        ctx.close()
+
+
 def test_plaintexts_match_oracle(small):
     c = small
     G = c.o.groups(c.B)
