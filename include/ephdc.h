@@ -173,6 +173,32 @@ ephdc_status ephdc_infer(ephdc_ctx* ctx, const int8_t* X_dev, const int8_t* Wt_d
                          const void* model_dev, const void* gk_dev, uint32_t* out_ct_dev,
                          void* stream);
 
+/* ---------------------------------------------------------------- batching */
+/* One client's queries: B rows of F int8 features at X_dev (B may be 0). */
+typedef struct {
+  const int8_t* X_dev;
+  int32_t B;
+} ephdc_request;
+
+/* Many clients' uneven batches in one pass (Sec. 3: batch inference fills the SIMD
+ * slots).  The requests are packed back to back into one query space of
+ * B = sum B_r <= max_batch queries: request r owns queries [off_r, off_r + B_r),
+ * off_r = sum_{r' < r} B_r', so its scores sit in groups off_r / cap ...; one pass
+ * reads the encrypted model once for all groups.  out_ct_dev: as ephdc_infer for B
+ * queries.  Each request's decrypted scores equal those of running it alone. */
+ephdc_status ephdc_infer_multi(ephdc_ctx* ctx, const ephdc_request* reqs, int32_t nreq,
+                               const int8_t* Wt_dev, const void* model_dev, const void* gk_dev,
+                               uint32_t* out_ct_dev, void* stream);
+
+/* Schedule knobs of the multi-accumulate (set by the autotuner; results never
+ * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled, "mac_min_groups" (tiled
+ * from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
+ * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
+ * warp, groups per CTA, plaintexts per staged chunk).  EPHDC_EINVAL for an unknown
+ * knob or an invalid value.  ephdc_tune_get returns -1 for an unknown knob. */
+ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);
+int64_t ephdc_tune_get(const ephdc_ctx* ctx, const char* knob);
+
 /* ---------------------------------------------------------------- host formats */
 /* Copy `count` device NTT-domain ciphertexts (e.g. the model, [2][L][n] each) to
  * the host in the coefficient domain, uint32 [count][2][L][n].  Synchronous. */

@@ -442,12 +442,27 @@ struct ephdc_ctx_impl;  // defined in host.cu
 
 // launch helpers implemented in the kernel translation units
 namespace ephdc {
+// X == NULL: the fp16 features are already in c.xh (see launch_gather_widen)
 cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt, int B,
                               int8_t* H, cudaStream_t st);
+// rows of up to 64 requests, packed back to back into c.xh (fp16)
+struct GatherTable {
+  const int8_t* ptr[64];
+  int32_t off[65];
+  int32_t count;
+};
+cudaError_t launch_gather_widen(const DevCtx& c, const GatherTable& t, cudaStream_t st);
 cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_t* pt,
                                 cudaStream_t st);
 cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                        uint32_t* partial, int splits, uint32_t* acc, cudaStream_t st);
+// tiling of the multi-group MAC: gt groups x ot outputs per warp, gc groups per
+// CTA, ic plaintext indices per shared-memory chunk
+struct MacTiling {
+  int gt, ot, gc, ic;
+};
+cudaError_t launch_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                             uint32_t* acc, const MacTiling& t, cudaStream_t st);
 cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
                               int count, const uint32_t* gk, cudaStream_t st);
 cudaError_t launch_export(const DevCtx& c, const uint32_t* acc, int count, uint32_t* out,

@@ -115,6 +115,12 @@ struct ephdc_ctx {
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
   uint64_t launches = 0;
+  // MAC schedule (autotuner knobs): mode 0 = automatic, 1 = streaming (split over
+  // plaintext ranges), 2 = tiled multi-group
+  int mac_mode = 0;
+  int mac_min_groups = 4;  // automatic mode: tiled from this many groups on
+  int mac_splits = 0;      // streaming: split count cap (0 = heuristic)
+  ephdc::MacTiling tile = {4, 8, 32, 8};
 };
 
 static cudaEvent_t take_event(ephdc_ctx* c) {
@@ -357,6 +363,17 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
     }
   }
 
+  // default tiling of the multi-group MAC: whole ciphertext columns per warp row
+  {
+    const int O = 2 * (int)d.Kp;
+    const int ot = O % 7 == 0 ? 7 : (O % 8 == 0 || O > 8 ? 8 : 4);
+    const int wo = (O + ot - 1) / ot;
+    int gt = 4, gc = (16 / (wo > 16 ? 16 : wo)) * gt;
+    if (gc > 32) gc = 32;
+    if (gc < gt) gt = gc = 2;
+    c->tile = {gt, ot, gc, 8};
+  }
+
   // scratch for batches up to max_batch
   c->G_max = (int)groups_for(c, (int32_t)p->max_batch);
   c->splits = mac_splits(d, 1);
@@ -491,8 +508,14 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
   const int G = (int)groups_for(c, B);
   cudaError_t e;
   {
-    StageTimer tm(c, EPHDC_STAGE_MAC, st, (2 * d.Kp + 3) / 4 + 1);
-    e = ephdc::launch_mac(d, pt, G, (const uint32_t*)model, c->partial, c->splits, c->acc, st);
+    const bool tiled = c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups);
+    StageTimer tm(c, EPHDC_STAGE_MAC, st, tiled ? 1 : (2 * d.Kp + 3) / 4 + 1);
+    if (tiled) {
+      e = ephdc::launch_mac_tiled(d, pt, G, (const uint32_t*)model, c->acc, c->tile, st);
+    } else {
+      const int cap = c->mac_splits > 0 && c->mac_splits < c->splits ? c->mac_splits : c->splits;
+      e = ephdc::launch_mac(d, pt, G, (const uint32_t*)model, c->partial, cap, c->acc, st);
+    }
   }
   if (e != cudaSuccess) return launched(c, e, "ptct_mac");
   const int count = G * (int)d.Kp;
@@ -682,6 +705,91 @@ ephdc_status ephdc_ntt_natural(ephdc_ctx* c, uint32_t limb, uint32_t* poly, int3
   if (limb > c->dc.L || count < 1) return fail(c, EPHDC_EINVAL, "bad limb or count");
   return launched(c, ephdc::launch_ntt_natural(c->dc, limb, poly, count, inverse,
                                                (cudaStream_t)stream), "ntt_natural");
+}
+
+ephdc_status ephdc_infer_multi(ephdc_ctx* c, const ephdc_request* reqs, int32_t nreq,
+                               const int8_t* Wt, const void* model, const void* gk, uint32_t* out,
+                               void* stream) {
+  CHECK_CTX(c);
+  if (!reqs || nreq < 1) return fail(c, EPHDC_EINVAL, "no requests");
+  CHECK_PTR(c, Wt, "Wt_dev");
+  CHECK_PTR(c, model, "model_dev");
+  CHECK_PTR(c, out, "out_ct_dev");
+  if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
+  int64_t total = 0;
+  for (int32_t r = 0; r < nreq; r++) {
+    if (reqs[r].B < 0) return fail(c, EPHDC_EINVAL, "request %d has a negative batch", r);
+    if (reqs[r].B > 0) CHECK_PTR(c, reqs[r].X_dev, "request X_dev");
+    total += reqs[r].B;
+  }
+  if (total < 1) return fail(c, EPHDC_EINVAL, "all requests are empty");
+  if (total > (int64_t)c->prm.max_batch)
+    return fail(c, EPHDC_ENOMEM, "packed batch %lld exceeds max_batch=%u", (long long)total,
+                c->prm.max_batch);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  {
+    StageTimer tm(c, EPHDC_STAGE_HDC, st, (uint64_t)((nreq + 63) / 64) + 3);
+    int32_t row = 0;
+    for (int32_t r0 = 0; r0 < nreq && e == cudaSuccess; r0 += 64) {
+      ephdc::GatherTable t;
+      t.count = 0;
+      t.off[0] = row;
+      for (int32_t r = r0; r < nreq && r < r0 + 64; r++) {
+        t.ptr[t.count] = reqs[r].X_dev;
+        row += reqs[r].B;
+        t.off[++t.count] = row;
+      }
+      e = ephdc::launch_gather_widen(c->dc, t, st);
+    }
+    if (e == cudaSuccess) e = ephdc::launch_hdc_encode(c->dc, nullptr, Wt, (int)total, c->H, st);
+  }
+  if (e != cudaSuccess) return launched(c, e, "hdc_encode");
+  {
+    StageTimer tm(c, EPHDC_STAGE_ENCODE, st, 1);
+    e = ephdc::launch_encode_plain(c->dc, c->H, (int)total, c->pt, st);
+  }
+  if (e != cudaSuccess) return launched(c, e, "encode_plain");
+  return similarity_impl(c, c->pt, (int32_t)total, model, gk, out, st);
+}
+
+ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
+  CHECK_CTX(c);
+  if (!knob) return fail(c, EPHDC_EINVAL, "knob is NULL");
+  const int O = 2 * (int)c->dc.Kp;
+  if (!strcmp(knob, "mac_mode")) {
+    if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1 or 2");
+    c->mac_mode = (int)v;
+  } else if (!strcmp(knob, "mac_min_groups")) {
+    if (v < 1) return fail(c, EPHDC_EINVAL, "mac_min_groups must be >= 1");
+    c->mac_min_groups = (int)v;
+  } else if (!strcmp(knob, "mac_splits")) {
+    if (v < 0) return fail(c, EPHDC_EINVAL, "mac_splits must be >= 0");
+    c->mac_splits = (int)v;
+  } else if (!strcmp(knob, "mac_tile")) {
+    // packed as gt * 1000000 + ot * 10000 + gc * 100 + ic
+    ephdc::MacTiling t = {(int)(v / 1000000), (int)(v / 10000 % 100), (int)(v / 100 % 100),
+                          (int)(v % 100)};
+    const int wo = (O + t.ot - 1) / (t.ot > 0 ? t.ot : 1);
+    const bool shape_ok = (t.gt == 2 || t.gt == 4) && (t.ot == 4 || t.ot == 7 || t.ot == 8);
+    if (!shape_ok || t.gc < t.gt || t.gc % t.gt || t.gc > 64 || (t.gc / t.gt) * wo > 16 ||
+        t.ic < 1 || 2 * (size_t)t.ic * (t.gc + O) * 128 > 227 * 1024)
+      return fail(c, EPHDC_EINVAL, "invalid MAC tiling %lld", (long long)v);
+    c->tile = t;
+  } else {
+    return fail(c, EPHDC_EINVAL, "unknown knob %s", knob);
+  }
+  return EPHDC_OK;
+}
+
+int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
+  if (!c || !knob) return -1;
+  if (!strcmp(knob, "mac_mode")) return c->mac_mode;
+  if (!strcmp(knob, "mac_min_groups")) return c->mac_min_groups;
+  if (!strcmp(knob, "mac_splits")) return c->mac_splits;
+  if (!strcmp(knob, "mac_tile"))
+    return (int64_t)c->tile.gt * 1000000 + c->tile.ot * 10000 + c->tile.gc * 100 + c->tile.ic;
+  return -1;
 }
 
 ephdc_status ephdc_device_status(ephdc_ctx* c) {

@@ -135,6 +135,110 @@ __global__ void __launch_bounds__(256) k_mac(DevCtx c, const uint32_t* __restric
   }
 }
 
+// Multi-group MAC: for each limb and coefficient k the accumulators form a small
+// matrix product Acc_k[g][o] = sum_i Pt_k[g][i] * C_k[i][o].  One CTA takes 32
+// consecutive coefficients of one limb, GC groups and all O outputs; P is walked in
+// chunks of IC plaintexts staged in shared memory with cp.async (double buffered),
+// so the model is read from HBM once per group block.  Warp (wg, wo) owns groups
+// wg*GT.. and outputs wo*OT..; its lanes are the 32 coefficients, so every shared
+// load is one conflict-free 128-byte row.
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+               "r"(ok ? 16 : 0));
+}
+
+template <int GT, int OT>
+__global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __restrict__ pt,
+                                                   const uint32_t* __restrict__ model,
+                                                   uint32_t* __restrict__ acc, int G, int GC,
+                                                   int IC) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const uint32_t l = blockIdx.y, k0 = blockIdx.x * 32;
+  const int g0 = blockIdx.z * GC;
+  const int O = 2 * (int)c.Kp;
+  const int WO = (O + OT - 1) / OT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wg = warp / WO, wo = warp - wg * WO;
+  const int rows = GC + O;                 // rows of 32 words per plaintext index
+  const int buf_words = IC * rows * 32;
+  const uint32_t p = c.mq[l].p;
+  const uint64_t mu = c.mq[l].mu;
+  const size_t n = c.n, L = c.L, P = c.P;
+
+  auto load_chunk = [&](int b, uint32_t i0) {
+    uint32_t* dst = sm + b * buf_words;
+    const int copies = IC * rows * 8;  // 16-byte pieces
+    for (int t = threadIdx.x; t < copies; t += blockDim.x) {
+      const int piece = t & 7, row = t >> 3;
+      const int ii = row / rows, rr = row - ii * rows;
+      const uint32_t i = i0 + ii;
+      const uint32_t* src;
+      bool ok = i < P;
+      if (rr < GC) {  // plaintext of group g0 + rr
+        const int g = g0 + rr;
+        ok = ok && g < G;
+        src = pt + (((size_t)(ok ? g : 0) * P + (ok ? i : 0)) * L + l) * n + k0 + piece * 4;
+      } else {        // model ciphertext output rr - GC
+        src = model + (((size_t)(ok ? i : 0) * O + (rr - GC)) * L + l) * n + k0 + piece * 4;
+      }
+      cp_async16_zfill(dst + row * 32 + piece * 4, src, ok);
+    }
+    asm volatile("cp.async.commit_group;\n");
+  };
+
+  uint64_t a[GT][OT];
+#pragma unroll
+  for (int x = 0; x < GT; x++)
+#pragma unroll
+    for (int y = 0; y < OT; y++) a[x][y] = 0;
+  const int gb = wg * GT, ob = wo * OT;
+  const int nchunks = (int)((P + IC - 1) / IC);
+  load_chunk(0, 0);
+  int cnt = 0;
+  for (int ch = 0; ch < nchunks; ch++) {
+    if (ch + 1 < nchunks) {
+      load_chunk((ch + 1) & 1, (ch + 1) * IC);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
+    __syncthreads();
+    const uint32_t* buf = sm + (ch & 1) * buf_words;
+    const int iend = min(IC, (int)P - ch * IC);
+    for (int ii = 0; ii < iend; ii++) {
+      const uint32_t* rowp = buf + ii * rows * 32 + lane;
+      uint32_t x[GT], y[OT];
+#pragma unroll
+      for (int g = 0; g < GT; g++) x[g] = rowp[(gb + g < GC ? gb + g : 0) * 32];
+#pragma unroll
+      for (int o = 0; o < OT; o++) y[o] = rowp[(GC + (ob + o < O ? ob + o : 0)) * 32];
+#pragma unroll
+      for (int g = 0; g < GT; g++)
+#pragma unroll
+        for (int o = 0; o < OT; o++) a[g][o] += (uint64_t)x[g] * y[o];
+      if (++cnt == 15) {
+        cnt = 0;
+#pragma unroll
+        for (int g = 0; g < GT; g++)
+#pragma unroll
+          for (int o = 0; o < OT; o++) a[g][o] = red64(a[g][o], p, mu);
+      }
+    }
+    __syncthreads();  // the buffer is refilled two chunks later
+  }
+#pragma unroll
+  for (int g = 0; g < GT; g++) {
+    const int gg = g0 + gb + g;
+    if (gb + g >= GC || gg >= G) continue;
+#pragma unroll
+    for (int o = 0; o < OT; o++) {
+      if (ob + o >= O) continue;
+      acc[(((size_t)gg * O + ob + o) * L + l) * n + k0 + lane] = red64(a[g][o], p, mu);
+    }
+  }
+}
+
 // acc[x] = sum_split partial[split][x] mod q_l, x over G*O*L*n words
 __global__ void k_mac_reduce(DevCtx c, const uint32_t* __restrict__ partial, int splits,
                              size_t words, uint32_t* __restrict__ acc) {
@@ -265,6 +369,35 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
     k_encode_plain<LG><<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
   });
   return cudaGetLastError();
+}
+
+// the tiled kernel's instantiations: (groups per warp, outputs per warp)
+template <int GT, int OT>
+static cudaError_t run_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                                 uint32_t* acc, int GC, int IC, cudaStream_t st) {
+  const int O = 2 * c.Kp;
+  const int warps = (GC / GT) * ((O + OT - 1) / OT);
+  const size_t smem = 2 * (size_t)IC * (GC + O) * 32 * sizeof(uint32_t);
+  if (warps < 1 || warps > 16 || GC % GT) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_mac_tiled<GT, OT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(c.n / 32, c.L, (G + GC - 1) / GC);
+  k_mac_tiled<GT, OT><<<grid, warps * 32, smem, st>>>(c, pt, model, acc, G, GC, IC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                             uint32_t* acc, const MacTiling& t, cudaStream_t st) {
+  switch (t.gt * 100 + t.ot) {
+    case 204: return run_mac_tiled<2, 4>(c, pt, G, model, acc, t.gc, t.ic, st);
+    case 207: return run_mac_tiled<2, 7>(c, pt, G, model, acc, t.gc, t.ic, st);
+    case 208: return run_mac_tiled<2, 8>(c, pt, G, model, acc, t.gc, t.ic, st);
+    case 404: return run_mac_tiled<4, 4>(c, pt, G, model, acc, t.gc, t.ic, st);
+    case 407: return run_mac_tiled<4, 7>(c, pt, G, model, acc, t.gc, t.ic, st);
+    case 408: return run_mac_tiled<4, 8>(c, pt, G, model, acc, t.gc, t.ic, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
 }
 
 cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,

@@ -227,6 +227,29 @@ __global__ void k_widen(const int8_t* __restrict__ src, __half* __restrict__ dst
   }
 }
 
+// int8 -> fp16 for the rows of up to 64 requests packed back to back: row
+// off[r] + j of the packed batch is row j of request r
+__global__ void k_gather_widen(const ephdc::GatherTable t, int F, __half* __restrict__ dst) {
+  const size_t per_row = (size_t)F / 16;
+  const size_t total = (size_t)(t.off[t.count] - t.off[0]) * per_row;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int row = t.off[0] + (int)(i / per_row);
+    const size_t col16 = i % per_row;
+    int r = 0;
+    while (r + 1 < t.count && t.off[r + 1] <= row) r++;
+    const int4 v = __ldg(reinterpret_cast<const int4*>(t.ptr[r] + (size_t)(row - t.off[r]) * F) +
+                         col16);
+    const int8_t* b = reinterpret_cast<const int8_t*>(&v);
+    __align__(16) __half h[16];
+#pragma unroll
+    for (int e = 0; e < 16; e++) h[e] = __short2half_rn((short)b[e]);
+    __half* d = dst + (size_t)row * F + 16 * col16;
+    reinterpret_cast<int4*>(d)[0] = reinterpret_cast<const int4*>(h)[0];
+    reinterpret_cast<int4*>(d)[1] = reinterpret_cast<const int4*>(h)[1];
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 cudaError_t tensor_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows,
@@ -254,12 +277,23 @@ cudaError_t tensor_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_
 
 namespace ephdc {
 
+static unsigned widen_blocks(size_t n) {
+  return (unsigned)((n + 255) / 256 < 2432 ? (n + 255) / 256 : 2432);
+}
+
+cudaError_t launch_gather_widen(const DevCtx& c, const GatherTable& t, cudaStream_t st) {
+  const size_t total = (size_t)(t.off[t.count] - t.off[0]) * c.F / 16;
+  if (total == 0) return cudaSuccess;
+  k_gather_widen<<<widen_blocks(total), 256, 0, st>>>(t, (int)c.F,
+                                                       reinterpret_cast<__half*>(c.xh));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt, int B,
                               int8_t* H, cudaStream_t st) {
   const size_t nx = (size_t)B * c.F / 16, nw = (size_t)c.D * c.F / 16;
-  auto blocks = [](size_t n) { return (unsigned)((n + 255) / 256 < 2432 ? (n + 255) / 256 : 2432); };
-  k_widen<<<blocks(nx), 256, 0, st>>>(X, reinterpret_cast<__half*>(c.xh), nx);
-  k_widen<<<blocks(nw), 256, 0, st>>>(Wt, reinterpret_cast<__half*>(c.wh), nw);
+  if (X) k_widen<<<widen_blocks(nx), 256, 0, st>>>(X, reinterpret_cast<__half*>(c.xh), nx);
+  k_widen<<<widen_blocks(nw), 256, 0, st>>>(Wt, reinterpret_cast<__half*>(c.wh), nw);
   CUtensorMap ta, tb;
   cudaError_t e = tensor_map(&ta, c.xh, c.F, (uint64_t)B, TM);
   if (e == cudaSuccess) e = tensor_map(&tb, c.wh, c.F, c.D, TN);

@@ -26,6 +26,10 @@ class EphdcError(RuntimeError):
         self.status = status
 
 
+class ephdc_request(ctypes.Structure):
+    _fields_ = [("X_dev", ctypes.c_void_p), ("B", ctypes.c_int32)]
+
+
 class ephdc_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("L", ctypes.c_uint32), ("k", ctypes.c_uint32),
                 ("k_in", ctypes.c_uint32), ("r", ctypes.c_uint32), ("D", ctypes.c_uint32),
@@ -61,6 +65,9 @@ _SIGS = {
     "bfv_ptct_similarity_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP,
                                                     _VP]),
     "ephdc_device_status": (ctypes.c_int, [_VP]),
+    "ephdc_infer_multi": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
+    "ephdc_tune_set": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int64]),
+    "ephdc_tune_get": (ctypes.c_int64, [_VP, ctypes.c_char_p]),
     "ephdc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ephdc_profile_read": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
 }
@@ -177,6 +184,18 @@ def ephdc_infer(ctx, X, Wt, B, model, gk, out_ct, stream=None):
                                   _ptr(gk, "gk"), _ptr(out_ct, "out_ct"), _stream(stream)))
 
 
+def ephdc_infer_multi(ctx, Xs, Wt, model, gk, out_ct, stream=None):
+    """Xs: list of int8 CUDA tensors [B_r][F] (one per client), packed back to back."""
+    arr = (ephdc_request * len(Xs))()
+    for r, X in enumerate(Xs):
+        B = X.shape[0]
+        arr[r].X_dev = _ptr(X, "X", dtype=torch.int8) if B else None
+        arr[r].B = B
+    _check(ctx, lib().ephdc_infer_multi(ctx, arr, len(Xs), _ptr(Wt, "Wt", dtype=torch.int8),
+                                        _ptr(model, "model"), _ptr(gk, "gk"),
+                                        _ptr(out_ct, "out_ct"), _stream(stream)))
+
+
 # ------------------------------------------------------------------ convenience
 class Context:
     """One set of BFV parameters + slot layout; allocates correctly sized tensors."""
@@ -250,6 +269,10 @@ class Context:
         bfv_ptct_similarity(self.ctx, pt, B, model, gk, out, stream)
         return out
 
+    def ptct_similarity_into(self, pt, B, model, gk, out, stream=None):
+        bfv_ptct_similarity(self.ctx, pt, B, model, gk, out, stream)
+        return out
+
     def infer(self, X, Wt, model, gk, out=None, stream=None):
         B = X.shape[0]
         out = self.out_ct(B) if out is None else out
@@ -289,6 +312,18 @@ class Context:
         _check(self.ctx, lib().ephdc_plain_to_host_coeff(self.ctx, _ptr(pt, "pt"), count,
                                                          host.ctypes.data_as(_VP)))
         return host
+
+    def infer_multi(self, Xs, Wt, model, gk, out=None, stream=None):
+        B = sum(int(X.shape[0]) for X in Xs)
+        out = self.out_ct(B) if out is None else out
+        ephdc_infer_multi(self.ctx, Xs, Wt, model, gk, out, stream)
+        return out
+
+    def tune_set(self, knob, value):
+        _check(self.ctx, lib().ephdc_tune_set(self.ctx, knob.encode(), int(value)))
+
+    def tune_get(self, knob):
+        return int(lib().ephdc_tune_get(self.ctx, knob.encode()))
 
     def device_status(self):
         """Raise EphdcError(EPHDC_ETIMEOUT) if a bounded device wait gave up."""

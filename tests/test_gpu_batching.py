@@ -1,0 +1,147 @@
+"""Batching of many clients' uneven batches: packing, the tiled multi-group
+multiply-accumulate, CUDA-graph replay and the autotuner, against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2511_00737_gb300 import autotune as AT
+from paper_2511_00737_gb300 import batching as BT
+from paper_2511_00737_gb300 import ephdc as E
+from paper_2511_00737_gb300 import workload as WL
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+# n, L, k, k_in, r, D, F, bits; cap = n / r for k_in = 1
+SMALL = dict(n=1024, L=3, k=3, k_in=1, r=4, D=100, F=32, bits=8)
+SIZES = [5, 0, 300, 17, 64, 1, 129]
+
+
+def _setup(sizes, seed=77, max_batch=None, **over):
+    prm = dict(SMALL, **over)
+    w = WL.Workload(name="t", B=sum(sizes), seed=seed, **prm)
+    ctx = E.Context(w.n, w.L, w.k, w.k_in, w.r, w.D, w.F, w.bits, w.shift,
+                    max_batch or max(1, w.B))
+    Xs = [WL.features(seed, b, w.F, batch=i) for i, b in enumerate(sizes)]
+    Wt = WL.projection(seed, w.D, w.F)
+    cls = WL.classes(seed, w.k, w.D)
+    sk, gk = ctx.keygen(seed)
+    model = ctx.encrypt_model(_dev(cls), sk, seed)
+    return w, ctx, Xs, Wt, cls, sk, gk, model
+
+
+def test_packed_requests_match_oracle_on_concatenated_batch():
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(SIZES)
+    out = ctx.infer_multi([_dev(x) for x in Xs], _dev(Wt), model, gk)
+    o = O.Oracle(w.n, w.L, w.k, w.k_in, w.r, w.D)
+    s, ogk = o.keygen(w.seed)
+    omodel = o.encrypt_model(w.seed, cls, s)
+    Xcat = np.concatenate(Xs)
+    H, _, oout = o.infer(Xcat, Wt, omodel, ogk, w.shift, w.bits)
+    assert np.array_equal(_u32(out).reshape(oout.shape), oout)
+    scores = _u32(ctx.decrypt_scores(sk, out, w.B))
+    assert np.array_equal(scores, O.clear_scores(H, cls))
+    ctx.device_status()
+    ctx.close()
+
+
+def test_each_request_same_alone_and_in_the_mix():
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(SIZES)
+    Wd = _dev(Wt)
+    mixed = ctx.infer_multi([_dev(x) for x in Xs], Wd, model, gk)
+    mixed_scores = _u32(ctx.decrypt_scores(sk, mixed, w.B))
+    pb = BT.PackedBatch(SIZES, ctx.cap)
+    for r, x in enumerate(Xs):
+        if not len(x):
+            continue
+        alone = ctx.infer(_dev(x), Wd, model, gk)
+        alone_scores = _u32(ctx.decrypt_scores(sk, alone, len(x)))
+        assert np.array_equal(mixed_scores[pb.rows(r)], alone_scores)
+        assert np.array_equal(alone_scores,
+                              O.clear_scores(O.hdc_encode(x, Wt, w.shift, w.bits), cls))
+    ctx.close()
+
+
+def test_tiled_mac_equals_streaming_for_every_tiling():
+    sizes = [900, 700, 1000, 33]  # 11 groups of 256
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(sizes, k=7, D=64)
+    H = ctx.hdc_encode(_dev(np.concatenate(Xs)), _dev(Wt))
+    pt = ctx.encode_plain(H)
+    ctx.tune_set("mac_mode", 1)
+    ref = ctx.ptct_similarity(pt, w.B, model, gk)
+    for knobs in AT.candidates(ctx, ctx.groups(w.B)):
+        AT.apply(ctx, {"mac_mode": 0, "mac_splits": 0, **knobs})
+        got = ctx.ptct_similarity(pt, w.B, model, gk)
+        assert torch.equal(got, ref), knobs
+    ctx.device_status()
+    ctx.close()
+
+
+def test_graph_replay_equals_eager_and_is_reused():
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(SIZES, max_batch=4 * 256)
+    Wd = _dev(Wt)
+    eager = BT.GraphedPipeline(ctx, Wd, model, gk, max_groups=4, use_graphs=False)
+    graphed = BT.GraphedPipeline(ctx, Wd, model, gk, max_groups=4, use_graphs=True)
+    mixes = [Xs, Xs[::-1], [Xs[2], Xs[6]], [Xs[2]]]
+    for mix in mixes:
+        dmix = [_dev(x) for x in mix]
+        a, pa = eager.run(dmix)
+        a = a.clone()
+        b, pb = graphed.run(dmix)
+        torch.cuda.synchronize()
+        assert pa.groups == pb.groups
+        assert torch.equal(a, b)
+        scores = _u32(ctx.decrypt_scores(sk, b, pb.total))
+        for r, x in enumerate(mix):
+            clear = O.clear_scores(O.hdc_encode(x, Wt, w.shift, w.bits), cls)
+            assert np.array_equal(scores[pb.rows(r)], clear)
+    assert set(graphed.graphs) == {2, 3}  # 516 queries need 3 groups of 256, 429 and 300 need 2
+    ctx.close()
+
+
+def test_autotuner_picks_a_schedule_and_results_do_not_change(tmp_path, monkeypatch):
+    monkeypatch.setattr(AT, "CACHE", str(tmp_path / "tune.json"))
+    sizes = [600, 600, 600]
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(sizes, k=2)
+    pt = ctx.encode_plain(ctx.hdc_encode(_dev(np.concatenate(Xs)), _dev(Wt)))
+    ctx.tune_set("mac_mode", 1)
+    ref = ctx.ptct_similarity(pt, w.B, model, gk)
+    best, ms, table = AT.tune_similarity(ctx, pt, w.B, model, gk, reps=2, max_candidates=12)
+    assert ms > 0 and len(table) == 12
+    assert torch.equal(ctx.ptct_similarity(pt, w.B, model, gk), ref)
+    best2, ms2, table2 = AT.tune_similarity(ctx, pt, w.B, model, gk)  # from the cache
+    assert best2 == best and table2 == []
+    ctx.close()
+
+
+@pytest.mark.slow
+def test_clients64_full_size_sampled():
+    """64 clients, log-uniform batch sizes (sum ~ 31.5K), F=768, D=10000, 4-bit HVs,
+    7 classes, n=8192, 4 primes: sampled queries' hypervectors and decrypted scores
+    against the oracle's projection and the clear dot products."""
+    w = WL.config("clients64")
+    ctx = E.Context.for_workload(w)
+    dev = torch.device("cuda")
+    Xs = [WL.features(w.seed, b, w.F, batch=i) for i, b in enumerate(w.clients)]
+    Wt = WL.projection(w.seed, w.D, w.F)
+    cls = WL.classes(w.seed, w.k, w.D)
+    sk, gk = ctx.keygen(w.seed)
+    model = ctx.encrypt_model(_dev(cls), sk, w.seed)
+    out = ctx.infer_multi([_dev(x) for x in Xs], _dev(Wt), model, gk)
+    scores = _u32(ctx.decrypt_scores(sk, out, w.B))
+    ctx.device_status()
+    Xcat = np.concatenate(Xs)
+    rng = np.random.default_rng(3)
+    rows = np.unique(np.concatenate([rng.integers(0, w.B, 256), [0, w.B - 1]]))
+    H = O.hdc_encode(Xcat[rows], Wt, w.shift, w.bits)
+    assert np.array_equal(scores[rows], O.clear_scores(H, cls))
+    ctx.close()
