@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-perquery", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="override the workload's batch size (profiling of smaller cases)")
     return ap.parse_args()
 
 
@@ -259,6 +261,20 @@ def run_ours(args, w, B):
     barrier()
     clk = clocks.stop()
     stage_ms, stage_calls, launches = ctx.profile_read()
+    if multi:
+        # graph replays record no stage events: take the stage breakdown and the
+        # launches per step from a few eager steps of the same packed work
+        pipe.use_graphs = False
+        ctx.profile_read()
+        ksteps_eager = 5
+        for i in range(ksteps_eager):
+            step(i)
+        torch.cuda.synchronize()
+        stage_ms, stage_calls, launches = ctx.profile_read()
+        stage_ms = {k: v * args.steps / ksteps_eager for k, v in stage_ms.items()}
+        stage_calls = {k: v * args.steps // ksteps_eager for k, v in stage_calls.items()}
+        launches = launches * args.steps // ksteps_eager
+        pipe.use_graphs = True
     ctx.profile(False)
     ms = maxall(e0.elapsed_time(e1)) / args.steps
     value = world * B / (ms / 1000.0)
@@ -392,6 +408,9 @@ def main():
     args = parse()
     from paper_2511_00737_gb300 import workload as WL
     w = WL.config(args.workload)
+    if args.batch:
+        w.B = args.batch
+        w.clients = []
     B = w.B
     if args.impl == "reference":
         run_reference(args, w, B)
