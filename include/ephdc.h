@@ -194,7 +194,7 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* ctx, const ephdc_request* reqs, int32_
  * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled, "mac_min_groups" (tiled
  * from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
  * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
- * warp, groups per CTA, plaintexts per staged chunk).  EPHDC_EINVAL for an unknown
+ * warp, groups per CTA, plaintexts per staged chunk, at most 15).  EPHDC_EINVAL for an unknown
  * knob or an invalid value.  ephdc_tune_get returns -1 for an unknown knob. */
 ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);
 int64_t ephdc_tune_get(const ephdc_ctx* ctx, const char* knob);

@@ -47,7 +47,7 @@ def candidates(ctx, G):
                 for gc in (8, 16, 32, 64):
                     if gc % gt or (gc // gt) * wo > 16 or gc > 2 * G + gt:
                         continue
-                    for ic in (4, 8, 16):
+                    for ic in (4, 8, 15):
                         if 2 * ic * (gc + O) * 128 > 227 * 1024:
                             continue
                         out.append({"mac_mode": 2,

@@ -773,7 +773,7 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     const int wo = (O + t.ot - 1) / (t.ot > 0 ? t.ot : 1);
     const bool shape_ok = (t.gt == 2 || t.gt == 4) && (t.ot == 4 || t.ot == 7 || t.ot == 8);
     if (!shape_ok || t.gc < t.gt || t.gc % t.gt || t.gc > 64 || (t.gc / t.gt) * wo > 16 ||
-        t.ic < 1 || 2 * (size_t)t.ic * (t.gc + O) * 128 > 227 * 1024)
+        t.ic < 1 || t.ic > 15 || 2 * (size_t)t.ic * (t.gc + O) * 128 > 227 * 1024)
       return fail(c, EPHDC_EINVAL, "invalid MAC tiling %lld", (long long)v);
     c->tile = t;
   } else {

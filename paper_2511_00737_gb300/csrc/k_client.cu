@@ -148,6 +148,13 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, boo
                "r"(ok ? 16 : 0));
 }
 
+// (hi:lo) += a * b as one carry chain: mad.lo.cc then madc.hi
+__device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, uint32_t b) {
+  asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;\n"
+      : "+r"(lo), "+r"(hi)
+      : "r"(a), "r"(b));
+}
+
 template <int GT, int OT>
 __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __restrict__ pt,
                                                    const uint32_t* __restrict__ model,
@@ -187,15 +194,17 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
     asm volatile("cp.async.commit_group;\n");
   };
 
-  uint64_t a[GT][OT];
+  // 64-bit accumulators as (lo, hi) words; each product (< 2^60) is added with a
+  // two-instruction carry chain, and the sums are reduced once per staged chunk
+  // (IC <= 15 products on top of a reduced value stay below 2^64)
+  uint32_t alo[GT][OT], ahi[GT][OT];
 #pragma unroll
   for (int x = 0; x < GT; x++)
 #pragma unroll
-    for (int y = 0; y < OT; y++) a[x][y] = 0;
+    for (int y = 0; y < OT; y++) alo[x][y] = ahi[x][y] = 0;
   const int gb = wg * GT, ob = wo * OT;
   const int nchunks = (int)((P + IC - 1) / IC);
   load_chunk(0, 0);
-  int cnt = 0;
   for (int ch = 0; ch < nchunks; ch++) {
     if (ch + 1 < nchunks) {
       load_chunk((ch + 1) & 1, (ch + 1) * IC);
@@ -206,6 +215,7 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
     __syncthreads();
     const uint32_t* buf = sm + (ch & 1) * buf_words;
     const int iend = min(IC, (int)P - ch * IC);
+#pragma unroll 3
     for (int ii = 0; ii < iend; ii++) {
       const uint32_t* rowp = buf + ii * rows * 32 + lane;
       uint32_t x[GT], y[OT];
@@ -216,15 +226,15 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
 #pragma unroll
       for (int g = 0; g < GT; g++)
 #pragma unroll
-        for (int o = 0; o < OT; o++) a[g][o] += (uint64_t)x[g] * y[o];
-      if (++cnt == 15) {
-        cnt = 0;
-#pragma unroll
-        for (int g = 0; g < GT; g++)
-#pragma unroll
-          for (int o = 0; o < OT; o++) a[g][o] = red64(a[g][o], p, mu);
-      }
+        for (int o = 0; o < OT; o++) mac64(alo[g][o], ahi[g][o], x[g], y[o]);
     }
+#pragma unroll
+    for (int g = 0; g < GT; g++)
+#pragma unroll
+      for (int o = 0; o < OT; o++) {
+        alo[g][o] = red64(((uint64_t)ahi[g][o] << 32) | alo[g][o], p, mu);
+        ahi[g][o] = 0;
+      }
     __syncthreads();  // the buffer is refilled two chunks later
   }
 #pragma unroll
@@ -234,7 +244,7 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
 #pragma unroll
     for (int o = 0; o < OT; o++) {
       if (ob + o >= O) continue;
-      acc[(((size_t)gg * O + ob + o) * L + l) * n + k0 + lane] = red64(a[g][o], p, mu);
+      acc[(((size_t)gg * O + ob + o) * L + l) * n + k0 + lane] = alo[g][o];
     }
   }
 }
@@ -375,7 +385,12 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
 template <int GT, int OT>
 static cudaError_t run_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                                  uint32_t* acc, int GC, int IC, cudaStream_t st) {
+  // IC <= 15 keeps (reduced value) + IC products below 2^64 between reductions
   const int O = 2 * c.Kp;
+  // no wider group block than the groups present
+  const int Gr = (G + GT - 1) / GT * GT;
+  if (GC > Gr) GC = Gr;
+  if (IC > 15) IC = 15;
   const int warps = (GC / GT) * ((O + OT - 1) / OT);
   const size_t smem = 2 * (size_t)IC * (GC + O) * 32 * sizeof(uint32_t);
   if (warps < 1 || warps > 16 || GC % GT) return cudaErrorInvalidConfiguration;
