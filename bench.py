@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-perquery", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
     return ap.parse_args()
@@ -404,6 +405,56 @@ def alu_peak_tbfly(pk):
     return 152 * 4 * 32 * mhz * 1e6 / 8 / 1e12
 
 
+def run_serve(args, w):
+    """Serving loop: Poisson arrivals (2000 requests/s), lognormal batch sizes (median
+    32, max 8192), continuous batching over two pipeline slots of up to 8 groups."""
+    import torch
+    from paper_2511_00737_gb300 import ephdc as E
+    from paper_2511_00737_gb300 import serving as SV
+    from paper_2511_00737_gb300 import workload as WL
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    seed = w.seed + 7919 * rank
+    keyctx = E.Context.for_workload(w, max_batch=1024)
+    sk, gk = keyctx.keygen(seed)
+    model = keyctx.encrypt_model(torch.from_numpy(WL.classes(seed, w.k, w.D)).to(dev), sk, seed)
+    Wt = torch.from_numpy(WL.projection(seed, w.D, w.F)).to(dev)
+    t, sizes = WL.arrivals(seed, args.serve_requests, rate_per_s=2000.0, median=32,
+                           max_batch=8192)
+    pool_rows = 65536
+    pool = torch.from_numpy(WL.features(seed, pool_rows, w.F)).to(dev)
+    offs = np.random.default_rng(seed).integers(0, pool_rows - 8192, len(sizes))
+    make_X = lambda rid: pool[offs[rid]:offs[rid] + int(sizes[rid])]
+    results = {}
+    for name, scale in (("poisson_2000_rps", 1.0), ("all_at_once", 0.0)):
+        srv = SV.Server(w, Wt, model, gk, slots=2, max_groups=8)
+        srv.warm()
+        wall = srv.run(t, make_X, time_scale=scale)
+        results[name] = srv.report(wall)
+        for s_ in srv.slots:
+            s_.ctx.close()
+        del srv
+        torch.cuda.synchronize()
+    live = results["poisson_2000_rps"]
+    offered = float(np.sum(sizes)) / float(t[-1])
+    if rank == 0:
+        line = {"metric": METRIC, "value": live["queries_per_s"], "unit": "queries/s",
+                "n_gpus": world, "steps": live["steps"], "warmup": 0,
+                "ms_per_step": 1e3 * live["wall_s"] / max(1, live["steps"]),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u32", "data": "synthetic",
+                "config": {"workload": "serve: %d requests, Poisson 2000 req/s, lognormal "
+                                       "batch (median 32, max 8192), F=%d, D=%d, k=%d, n=%d, "
+                                       "L=%d, layout k_in=%d r=%d; 2 slots x 8 groups" % (
+                                           len(sizes), w.F, w.D, w.k, w.n, w.L, w.k_in, w.r),
+                           "offered_queries_per_s": offered},
+                "serving": results}
+        print(json.dumps(line), flush=True)
+    keyctx.close()
+
+
 def main():
     args = parse()
     from paper_2511_00737_gb300 import workload as WL
@@ -413,7 +464,9 @@ def main():
         w.clients = []
     B = w.B
     if args.impl == "reference":
-        run_reference(args, w, B)
+        run_reference(args, w, B if B else 1024)
+    elif args.workload == "serve" and not args.batch:
+        run_serve(args, w)
     else:
         run_ours(args, w, B)
 

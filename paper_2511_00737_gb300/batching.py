@@ -94,3 +94,18 @@ class GraphedPipeline:
         else:
             self._launch(pb.groups)
         return self.out[:pb.groups * self.ct_words], pb
+
+    def launch(self, Xs, stream):
+        """Packs and runs one step entirely on `stream`, with no synchronisation with
+        other streams (the graph for the step's group count must already exist or is
+        captured first).  Returns (score ciphertexts of the G groups, PackedBatch)."""
+        if self.use_graphs:
+            pb = PackedBatch([x.shape[0] for x in Xs], self.cap)
+            self.graph(pb.groups)
+        with torch.cuda.stream(stream):
+            pb = self.pack(Xs)
+            if self.use_graphs:
+                self.graphs[pb.groups].replay()
+            else:
+                self._launch(pb.groups)
+        return self.out[:pb.groups * self.ct_words], pb

@@ -1,0 +1,183 @@
+"""Continuous-batching serving loop for client-side encrypted HDC inference.
+
+Requests (one client's batch of feature rows each) arrive over time.  The loop
+- admits an arriving request while its device bytes (its features plus its share
+  of the score ciphertexts) fit in a device-memory budget that excludes the
+  resident encrypted model and rotation keys; a request larger than the whole
+  budget is rejected, the others wait in arrival order until memory frees up;
+- whenever one of its pipeline slots is idle, packs the admitted requests (up to
+  the slot's group capacity) into one step and launches it on the slot's stream;
+  each slot has its own context scratch, CUDA stream and CUDA graphs, and all slots
+  share the device-resident model and keys, so a step can run on the device while
+  the next one is being packed and launched;
+- when a step's score ciphertexts have reached host memory (the message to the
+  server, Sec. 4.1), completes its requests, frees their memory and records each
+  request's latency from arrival to completion.
+
+Each request's result is the range of packed queries it owns in its step's score
+ciphertexts; decrypting them gives the same scores as running the request alone.
+"""
+import collections
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import batching as BT
+from . import ephdc as E
+
+
+class Request:
+    __slots__ = ("rid", "arrival", "X", "B", "admitted", "launched", "done", "step",
+                 "rows", "nbytes")
+
+    def __init__(self, rid, arrival, X):
+        self.rid, self.arrival, self.X = rid, arrival, X
+        self.B = int(X.shape[0])
+        self.admitted = self.launched = self.done = None
+        self.step = None
+        self.rows = None
+        self.nbytes = 0
+
+
+class Step:
+    """One launched packed step: its requests, host copy of the ciphertexts, event."""
+
+    def __init__(self, sid, reqs, packed, host_out, event, slot):
+        self.sid, self.reqs, self.packed = sid, reqs, packed
+        self.host_out, self.event, self.slot = host_out, event, slot
+
+
+class Slot:
+    def __init__(self, w, Wt, model, gk, max_groups, use_graphs=True):
+        cap = 2 * ((w.n // (2 * w.r)) // w.k_in)
+        self.ctx = E.Context.for_workload(w, max_batch=max_groups * cap)
+        self.pipe = BT.GraphedPipeline(self.ctx, Wt, model, gk, max_groups=max_groups,
+                                       use_graphs=use_graphs)
+        self.stream = torch.cuda.Stream(device=self.ctx.device)
+        self.busy = None
+
+    def warm(self):
+        for G in range(1, self.pipe.max_groups + 1):
+            self.pipe.graph(G) if self.pipe.use_graphs else None
+        torch.cuda.synchronize()
+
+
+class Server:
+    def __init__(self, w, Wt, model, gk, slots=2, max_groups=8, budget_bytes=None,
+                 use_graphs=True, keep_outputs=False):
+        self.w = w
+        self.cap = 2 * ((w.n // (2 * w.r)) // w.k_in)
+        self.ct_bytes = 2 * w.L * w.n * 4
+        self.Kp = w.k // w.k_in
+        self.slots = [Slot(w, Wt, model, gk, max_groups, use_graphs) for _ in range(slots)]
+        self.max_queries = max_groups * self.cap
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            budget_bytes = max(0, free - (4 << 30))
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.keep_outputs = keep_outputs
+        self.pending = collections.deque()   # arrived, not admitted (memory)
+        self.queue = collections.deque()     # admitted, not launched
+        self.steps = []
+        self.completed = []
+        self.rejected = []
+
+    def request_bytes(self, B):
+        # the request's features on the device plus its share of score ciphertexts
+        return B * self.w.F + math.ceil(B / self.cap) * self.Kp * self.ct_bytes
+
+    def warm(self):
+        for s in self.slots:
+            s.warm()
+
+    # ------------------------------------------------------------------ events
+    def arrive(self, req, now):
+        req.nbytes = self.request_bytes(req.B)
+        if req.nbytes > self.budget or req.B > self.max_queries:
+            req.done = now
+            self.rejected.append(req)
+            return
+        self.pending.append(req)
+        self._admit(now)
+
+    def _admit(self, now):
+        while self.pending and self.used + self.pending[0].nbytes <= self.budget:
+            r = self.pending.popleft()
+            self.used += r.nbytes
+            r.admitted = now
+            self.queue.append(r)
+
+    def _launch(self, slot, now):
+        take, total = [], 0
+        while self.queue and total + self.queue[0].B <= self.max_queries:
+            r = self.queue.popleft()
+            take.append(r)
+            total += r.B
+        if not take:
+            return False
+        with torch.cuda.stream(slot.stream):
+            out, pb = slot.pipe.launch([r.X for r in take], slot.stream)
+            host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+            host.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(slot.stream)
+        st = Step(len(self.steps), take, pb, host, ev, slot)
+        for i, r in enumerate(take):
+            r.launched, r.step, r.rows = now, st.sid, pb.rows(i)
+        self.steps.append(st)
+        slot.busy = st
+        return True
+
+    def poll(self, now):
+        """Completes finished steps, admits, launches on idle slots.  Returns True if
+        anything is still queued or in flight."""
+        for slot in self.slots:
+            st = slot.busy
+            if st is not None and st.event.query():
+                t = time.perf_counter() if now is None else now
+                for r in st.reqs:
+                    r.done = t
+                    self.used -= r.nbytes
+                    self.completed.append(r)
+                if not self.keep_outputs:
+                    st.host_out = None
+                slot.busy = None
+        self._admit(now)
+        for slot in self.slots:
+            if slot.busy is None and self.queue:
+                self._launch(slot, now)
+        return bool(self.queue or self.pending or any(s.busy for s in self.slots))
+
+    # ------------------------------------------------------------------ driver
+    def run(self, arrivals, make_X, time_scale=1.0):
+        """Replays an arrival schedule in real time (arrival times in seconds,
+        multiplied by time_scale) and serves it to completion."""
+        order = np.argsort(arrivals, kind="stable")
+        t0 = time.perf_counter()
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(order) and arrivals[order[nxt]] * time_scale <= now:
+                rid = int(order[nxt])
+                self.arrive(Request(rid, arrivals[rid] * time_scale, make_X(rid)), now)
+                nxt += 1
+            busy = self.poll(time.perf_counter() - t0)
+            if nxt >= len(order) and not busy:
+                break
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    def report(self, wall_s):
+        lat = np.array([r.done - r.arrival for r in self.completed]) if self.completed else \
+            np.zeros(1)
+        q = sum(r.B for r in self.completed)
+        return {"requests": len(self.completed) + len(self.rejected),
+                "completed": len(self.completed), "rejected": len(self.rejected),
+                "queries": q, "queries_per_s": q / wall_s if wall_s > 0 else 0.0,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "steps": len(self.steps),
+                "mean_queries_per_step": q / max(1, len(self.steps)), "wall_s": wall_s}
