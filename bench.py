@@ -235,12 +235,10 @@ def run_ours(args, w, B):
         if dist is not None:
             dist.barrier()
 
+    from paper_2511_00737_gb300 import replicas as RP
+
     def maxall(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return RP.max_over_ranks(v, device=dev)
 
     st = torch.cuda.current_stream()
     for i in range(args.warmup):
@@ -277,8 +275,8 @@ def run_ours(args, w, B):
         launches = launches * args.steps // ksteps_eager
         pipe.use_graphs = True
     ctx.profile(False)
-    ms = maxall(e0.elapsed_time(e1)) / args.steps
-    value = world * B / (ms / 1000.0)
+    value, ms_total = RP.job_throughput(B * args.steps, e0.elapsed_time(e1), world, device=dev)
+    ms = ms_total / args.steps
 
     # end to end: pinned host inputs in, score ciphertexts back to pinned host
     ksteps = max(1, min(args.steps, 300))
