@@ -191,8 +191,9 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* ctx, const ephdc_request* reqs, int32_
                                uint32_t* out_ct_dev, void* stream);
 
 /* Schedule knobs of the multi-accumulate (set by the autotuner; results never
- * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled, "mac_min_groups" (tiled
- * from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
+ * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled / 3 tensor cores (exact
+ * byte split, k/k_in <= 16), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
+ * cores from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
  * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
  * warp, groups per CTA, plaintexts per staged chunk, at most 15).  EPHDC_EINVAL for an unknown
  * knob or an invalid value.  ephdc_tune_get returns -1 for an unknown knob. */

@@ -5,8 +5,8 @@ bfv_ptct_similarity on the device with CUDA events (the result never changes,
 only the speed), applies the fastest and remembers it in a JSON cache keyed by
 GPU, ring degree, limbs, layout and G.  Candidates: the streaming kernel split
 over plaintext ranges (several split caps), and the tiled multi-group kernel with
-2 or 4 groups and 4, 7 or 8 outputs per warp, 8 to 64 groups per CTA and 4 to 16
-plaintexts per staged chunk.
+2 or 4 groups and 4, 7 or 8 outputs per warp, 8 to 64 groups per CTA and 4 to 15
+plaintexts per staged chunk, and the exact byte-split product on the tensor cores.
 """
 import json
 import os
@@ -40,6 +40,8 @@ def _save(d):
 def candidates(ctx, G):
     O = 2 * ctx.Kp
     out = [{"mac_mode": 1, "mac_splits": s} for s in (0, 8, 16, 32)]
+    if G >= 2 and O <= 32:
+        out.append({"mac_mode": 3})
     if G >= 2:
         for gt in (2, 4):
             for ot in (4, 7, 8):

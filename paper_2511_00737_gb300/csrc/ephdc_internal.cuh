@@ -463,6 +463,9 @@ struct MacTiling {
 };
 cudaError_t launch_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                              uint32_t* acc, const MacTiling& t, cudaStream_t st);
+// the same accumulators through the exact byte-split tensor-core product (k/k_in <= 16)
+cudaError_t launch_mac_tc(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                          uint32_t* acc, cudaStream_t st);
 cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
                               int count, const uint32_t* gk, cudaStream_t st);
 cudaError_t launch_export(const DevCtx& c, const uint32_t* acc, int count, uint32_t* out,

@@ -119,6 +119,7 @@ struct ephdc_ctx {
   // plaintext ranges), 2 = tiled multi-group
   int mac_mode = 0;
   int mac_min_groups = 4;  // automatic mode: tiled from this many groups on
+  int mac_tc_min_groups = 8;  // automatic mode: tensor cores from this many groups on
   int mac_splits = 0;      // streaming: split count cap (0 = heuristic)
   ephdc::MacTiling tile = {4, 8, 32, 8};
 };
@@ -508,9 +509,16 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
   const int G = (int)groups_for(c, B);
   cudaError_t e;
   {
-    const bool tiled = c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups);
-    StageTimer tm(c, EPHDC_STAGE_MAC, st, tiled ? 1 : (2 * d.Kp + 3) / 4 + 1);
-    if (tiled) {
+    const bool tc_ok = 2 * d.Kp <= 32;
+    const bool tc = tc_ok && (c->mac_mode == 3 ||
+                              (c->mac_mode == 0 && G >= c->mac_tc_min_groups));
+    const bool tiled = !tc && (c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups));
+    StageTimer tm(c, EPHDC_STAGE_MAC, st, tc || tiled ? 1 : (2 * d.Kp + 3) / 4 + 1);
+    if (c->mac_mode == 3 && !tc_ok) {
+      e = cudaErrorNotSupported;
+    } else if (tc) {
+      e = ephdc::launch_mac_tc(d, pt, G, (const uint32_t*)model, c->acc, st);
+    } else if (tiled) {
       e = ephdc::launch_mac_tiled(d, pt, G, (const uint32_t*)model, c->acc, c->tile, st);
     } else {
       const int cap = c->mac_splits > 0 && c->mac_splits < c->splits ? c->mac_splits : c->splits;
@@ -758,8 +766,12 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
   if (!knob) return fail(c, EPHDC_EINVAL, "knob is NULL");
   const int O = 2 * (int)c->dc.Kp;
   if (!strcmp(knob, "mac_mode")) {
-    if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1 or 2");
+    if (v < 0 || v > 3) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1, 2 or 3");
+    if (v == 3 && O > 32) return fail(c, EPHDC_EUNSUPPORTED, "tensor-core MAC needs k/k_in <= 16");
     c->mac_mode = (int)v;
+  } else if (!strcmp(knob, "mac_tc_min_groups")) {
+    if (v < 1) return fail(c, EPHDC_EINVAL, "mac_tc_min_groups must be >= 1");
+    c->mac_tc_min_groups = (int)v;
   } else if (!strcmp(knob, "mac_min_groups")) {
     if (v < 1) return fail(c, EPHDC_EINVAL, "mac_min_groups must be >= 1");
     c->mac_min_groups = (int)v;
@@ -786,6 +798,7 @@ int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
   if (!c || !knob) return -1;
   if (!strcmp(knob, "mac_mode")) return c->mac_mode;
   if (!strcmp(knob, "mac_min_groups")) return c->mac_min_groups;
+  if (!strcmp(knob, "mac_tc_min_groups")) return c->mac_tc_min_groups;
   if (!strcmp(knob, "mac_splits")) return c->mac_splits;
   if (!strcmp(knob, "mac_tile"))
     return (int64_t)c->tile.gt * 1000000 + c->tile.ot * 10000 + c->tile.gc * 100 + c->tile.ic;

@@ -1,0 +1,343 @@
+// Dense multiply-accumulate of many groups on the tensor cores (the batch x classes
+// contraction of Sec. 4.1's HE compute when many query groups share the model):
+//   Acc_k[g][o] = sum_i Pt_k[g][i] * C_k[i][o]  (mod q_l)   for every coefficient k.
+//
+// Exact byte split: residues < 2^30 are written as 4 bytes, a = sum_u a_u 2^(8u),
+// c = sum_v c_v 2^(8v), so sum_i a c = sum_{u,v} 2^(8(u+v)) S_uv with
+// S_uv = sum_i a_u c_v.  Per coefficient one MMA computes every S_uv at once:
+// rows (u, g) of the digit matrix A' (4 GP x K) times columns (v, o) of B' (K x 4 OP).
+// Bytes are fp16 values, products are < 2^16, and a window of 256 plaintexts keeps
+// every fp32 partial sum below 2^24: exact.  After each window the TMEM accumulator
+// is read out, recombined with 2^(8(u+v)) mod q_l and added to 64-bit shared
+// accumulators; the next window restarts the MMA accumulation.
+//
+// One CTA: limb l, KB consecutive coefficients, one block of GP groups, all outputs.
+// Per 16-plaintext chunk: cp.async stages the raw residues (rows of KB words) into a
+// 4-deep ring; 8 warps split them into fp16 digits laid out as the MMA's canonical
+// K-major, no-swizzle operand tiles (double buffered); one thread issues
+// tcgen05.mma (M = 128, N = 4 OP, K = 16) per coefficient and M tile, and commits to
+// the buffer's mbarrier.  All waits are bounded.
+#include <cuda_fp16.h>
+
+#include "ephdc_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status,
+                                          uint32_t code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1ll << 31)) {
+      atomicCAS(status, 0u, code);
+      return false;
+    }
+  }
+  return true;
+}
+// shared-memory descriptor, K-major without swizzle: 8-row x 16-byte core matrices,
+// LBO = byte stride between core matrices along K, SBO = along M/N; version 1
+__device__ __forceinline__ uint64_t sdesc_noswz(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+template <uint32_t IDESC>
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]),
+        "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]),
+        "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool ok) {
+  const uint32_t d = smem_u32(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(d), "l"(src), "n"(BYTES),
+               "r"(ok ? BYTES : 0));
+}
+// byte u of x and of y as the two fp16 halves (exact integers 0..255): the bytes land
+// in the mantissas of 1024.0 (0x6400), and 1024 is subtracted again
+__device__ __forceinline__ uint32_t digit_pair(uint32_t x, uint32_t y, uint32_t u) {
+  const uint32_t t = __byte_perm(x, y, u | ((u + 4) << 8));  // bytes [x_u, x_0, y_u, x_0]
+  uint32_t h = (t & 0x00FF00FFu) | 0x64006400u;
+  __half2 v = *reinterpret_cast<const __half2*>(&h);
+  v = __hsub2(v, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+}  // namespace
+
+namespace {
+
+// byte offset of element (row r, k) in a K-major, no-swizzle operand tile of K = 16:
+// core matrices of 8 rows x 8 halves (128 B), the two K-adjacent cores 128 B apart
+// (LBO), consecutive 8-row groups 256 B apart (SBO)
+__device__ __forceinline__ uint32_t op_off(uint32_t r, uint32_t k) {
+  return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+template <int MT, int OP, int KB>
+struct TcCfg {
+  static constexpr int GP = 32 * MT;               // groups per CTA: A rows (u, g) = 128 MT
+  static constexpr int N = 4 * OP;                 // MMA N: columns (v, o)
+  static constexpr int KC = 16;                    // plaintexts per chunk = one MMA K step
+  static constexpr int WIN = 16;                   // chunks per exact window (256 plaintexts)
+  static constexpr int RING = MT == 1 ? 3 : 4;     // cp.async stages of raw residues
+  static constexpr int ROWS = GP + OP;             // raw rows per chunk
+  static constexpr int PAD = KB == 2 ? 16 : 4;     // row padding (words): conflict-free reads
+  static constexpr int RSTRIDE = KC * KB + PAD;    // words per raw row
+  static constexpr int RAW_WORDS = ROWS * RSTRIDE;
+  static constexpr int A_BYTES = 4 * GP * KC * 2;  // per coefficient
+  static constexpr int B_BYTES = N * KC * 2;
+  static constexpr int OPS_BYTES = KB * (A_BYTES + B_BYTES);  // one operand buffer
+  static constexpr int TCOLS = KB * MT * N;                   // TMEM columns
+  static constexpr uint32_t IDESC =
+      (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  static constexpr size_t SMEM =
+      1024 + 2 * OPS_BYTES + RING * RAW_WORDS * 4 + KB * GP * OP * 8 + 64;
+};
+
+template <int MT, int OP, int KB>
+__global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __restrict__ pt,
+                                                   const uint32_t* __restrict__ model,
+                                                   uint32_t* __restrict__ out, int G,
+                                                   uint32_t* status) {
+  using C = TcCfg<MT, OP, KB>;
+  constexpr int GP = C::GP, N = C::N, KC = C::KC;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* ops = sm;                                                // [2][KB][A | B]
+  uint32_t* raw = (uint32_t*)(sm + 2 * C::OPS_BYTES);               // [RING][ROWS][RSTRIDE]
+  unsigned long long* accs = (unsigned long long*)(raw + C::RING * C::RAW_WORDS);  // [KB][GP][OP]
+  uint64_t* bars = (uint64_t*)(accs + KB * GP * OP);                // MMA done, per buffer
+  uint32_t* tslot = (uint32_t*)(bars + 2);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t l = blockIdx.y, k0 = blockIdx.x * KB;
+  const int g0 = blockIdx.z * GP;
+  const int O = 2 * (int)c.Kp;
+  const uint32_t P = c.P, n = c.n, L = c.L;
+  const ModP m = c.mq[l];
+  const int nch = (int)((P + KC - 1) / KC);
+
+  for (int i = tid; i < KB * GP * OP; i += blockDim.x) accs[i] = 0;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tslot)),
+                 "n"(C::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  // raw residues of chunk ch: rows g (plaintexts of group g0 + g) and GP + o (model
+  // output o), each KC plaintexts x KB coefficients; zero outside the batch
+  auto load_raw = [&](int ch, int stage) {
+    uint32_t* dst = raw + stage * C::RAW_WORDS;
+    for (int t = tid; t < C::ROWS * KC; t += blockDim.x) {
+      const int row = t / KC, ii = t - row * KC;
+      const uint32_t i = (uint32_t)ch * KC + ii;
+      bool ok = i < P;
+      const uint32_t* src;
+      if (row < GP) {
+        const int g = g0 + row;
+        ok = ok && g < G;
+        src = pt + (((size_t)(ok ? g : 0) * P + (ok ? i : 0)) * L + l) * n + k0;
+      } else {
+        const int o = row - GP;
+        ok = ok && o < O;
+        src = model + (((size_t)(ok ? i : 0) * O + (ok ? o : 0)) * L + l) * n + k0;
+      }
+      cp_async<KB * 4>(dst + row * C::RSTRIDE + ii * KB, src, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  // raw stage -> fp16 digit operand tiles of every coefficient (buffer `buf`)
+  auto transform = [&](int stage, int buf) {
+    const uint32_t* rs = raw + stage * C::RAW_WORDS;
+    uint8_t* ob = ops + buf * C::OPS_BYTES;
+    const int glo = lane >> 2, kp = lane & 3;
+    constexpr int AITEMS = (GP / 8) * 2, ITEMS = AITEMS + (OP / 8) * 2;
+    for (int it = warp; it < ITEMS; it += blockDim.x / 32) {
+      const bool isA = it < AITEMS;
+      const int jt = isA ? it : it - AITEMS;
+      const int hi = jt >> 1, cc = jt & 1;
+      const int rr = hi * 8 + glo;                 // group g or output o
+      const int ii = cc * 8 + 2 * kp;              // K pair (ii, ii + 1)
+      const uint32_t* w = rs + (isA ? rr : GP + rr) * C::RSTRIDE + ii * KB;
+      uint32_t x[KB], y[KB];
+#pragma unroll
+      for (int j = 0; j < KB; j++) {
+        x[j] = w[j];
+        y[j] = w[KB + j];
+      }
+#pragma unroll
+      for (int j = 0; j < KB; j++) {
+        uint8_t* tile = ob + j * (C::A_BYTES + C::B_BYTES) + (isA ? 0 : C::A_BYTES);
+        const int stride = isA ? GP : OP;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          *reinterpret_cast<uint32_t*>(tile + op_off(u * stride + rr, ii)) =
+              digit_pair(x[j], y[j], u);
+      }
+    }
+  };
+
+  uint32_t W[7];  // 2^(8e) mod q_l
+  W[0] = 1;
+#pragma unroll
+  for (int e = 1; e < 7; e++) W[e] = mulm(W[e - 1], 256u, m);
+
+  for (int s = 0; s < C::RING - 1; s++) {
+    if (s < nch) load_raw(s, s);
+    else asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
+  bool alive = true;
+  for (int ch = 0; ch < nch; ch++) {
+    const int buf = ch & 1;
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(C::RING - 2) : "memory");
+    __syncthreads();
+    {
+      const int nx = ch + C::RING - 1;
+      if (nx < nch) load_raw(nx, nx % C::RING);
+      else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    bool ok = true;
+    if (ch >= 2) ok = mbar_wait(smem_u32(&bars[buf]), ((ch - 2) >> 1) & 1, status, 11);
+    if (ok && alive) transform(ch % C::RING, buf);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    alive = __syncthreads_and(alive && ok);
+    if (tid == 0 && alive) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const uint32_t ob = smem_u32(ops + buf * C::OPS_BYTES);
+#pragma unroll
+      for (int j = 0; j < KB; j++) {
+        const uint32_t a0 = ob + j * (C::A_BYTES + C::B_BYTES), b0 = a0 + C::A_BYTES;
+        const uint64_t bd = sdesc_noswz(b0, 128, 256);
+#pragma unroll
+        for (int mt = 0; mt < MT; mt++)
+          tc_mma<C::IDESC>(tmem + (j * MT + mt) * N, sdesc_noswz(a0 + mt * 4096, 128, 256), bd,
+                           (ch % C::WIN) != 0);
+      }
+      tc_commit(smem_u32(&bars[buf]));
+    }
+    if ((ch % C::WIN) == C::WIN - 1 || ch == nch - 1) {
+      // window complete: every S_uv of these 256 plaintexts is in TMEM
+      ok = alive && mbar_wait(smem_u32(&bars[buf]), (ch >> 1) & 1, status, 12);
+      alive = __syncthreads_and(ok);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (alive) {
+        const int q = warp & 3, h = warp >> 2;
+#pragma unroll 1
+        for (int j = 0; j < KB; j++)
+#pragma unroll 1
+          for (int mt = 0; mt < MT; mt++) {
+            const int r = mt * 128 + 32 * q + lane;
+            const int u = r / GP, g = r - u * GP;
+            const bool row_ok = g0 + g < G;
+#pragma unroll 1
+            for (int x = 0; x < N / 64; x++) {
+              uint32_t v[32];
+              const int col0 = h * (N / 2) + x * 32;
+              tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (j * MT + mt) * N + col0, v);
+              if (row_ok) {
+#pragma unroll
+                for (int e = 0; e < 32; e++) {
+                  const int col = col0 + e, vv = col / OP, o = col - vv * OP;
+                  if (o < O) {
+                    const uint32_t s = (uint32_t)__float2uint_rz(__uint_as_float(v[e]));
+                    atomicAdd(&accs[(j * GP + g) * OP + o],
+                              (unsigned long long)mulm(s, W[u + vv], m));
+                  }
+                }
+              }
+            }
+          }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int idx = tid; idx < KB * GP * OP; idx += blockDim.x) {
+    const int j = idx % KB, rest = idx / KB;
+    const int o = rest % OP, g = rest / OP;
+    if (g0 + g < G && o < O)
+      out[(((size_t)(g0 + g) * O + o) * L + l) * n + k0 + j] =
+          red64(accs[(j * GP + g) * OP + o], m.p, m.mu);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "n"(C::TCOLS)
+                 : "memory");
+}
+
+template <int MT, int OP, int KB>
+cudaError_t run_mac_tc(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                       uint32_t* acc, cudaStream_t st) {
+  using C = TcCfg<MT, OP, KB>;
+  cudaError_t e = cudaFuncSetAttribute(k_mac_tc<MT, OP, KB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid(c.n / KB, c.L, (G + C::GP - 1) / C::GP);
+  k_mac_tc<MT, OP, KB><<<grid, 256, C::SMEM, st>>>(c, pt, model, acc, G, c.status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace ephdc {
+
+cudaError_t launch_mac_tc(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
+                          uint32_t* acc, cudaStream_t st) {
+  const int O = 2 * (int)c.Kp;
+  if (O > 32) return cudaErrorNotSupported;
+  const bool two = G > 32;  // 64 groups per CTA (two M tiles) beyond 32 groups
+  if (O <= 16) return two ? run_mac_tc<2, 16, 4>(c, pt, G, model, acc, st)
+                          : run_mac_tc<1, 16, 4>(c, pt, G, model, acc, st);
+  return two ? run_mac_tc<2, 32, 2>(c, pt, G, model, acc, st)
+             : run_mac_tc<1, 32, 2>(c, pt, G, model, acc, st);
+}
+
+}  // namespace ephdc

@@ -145,3 +145,27 @@ def test_clients64_full_size_sampled():
     H = O.hdc_encode(Xcat[rows], Wt, w.shift, w.bits)
     assert np.array_equal(scores[rows], O.clear_scores(H, cls))
     ctx.close()
+
+
+@pytest.mark.parametrize("k,groups,D", [
+    (7, 11, 1200),   # 14 outputs: one M tile, N = 64; P = 300: two 256-windows, ragged K
+    (5, 40, 300),    # 10 outputs, 40 groups: two M tiles (64 groups per CTA), N = 64
+    (16, 9, 520),    # 32 outputs: N = 128, two coefficients per CTA
+    (16, 70, 64),    # 32 outputs, 70 groups: two group blocks of two M tiles
+])
+def test_tensor_core_mac_equals_streaming(k, groups, D):
+    """The exact byte-split tensor-core product gives the same accumulators (and so the
+    same score ciphertexts) as the 64-bit CUDA-core multiply-accumulate."""
+    sizes = [256] * groups
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(sizes, k=k, D=D)
+    pt = ctx.encode_plain(ctx.hdc_encode(_dev(np.concatenate(Xs)), _dev(Wt)))
+    ctx.tune_set("mac_mode", 1)
+    ref = ctx.ptct_similarity(pt, w.B, model, gk)
+    ctx.tune_set("mac_mode", 3)
+    got = ctx.ptct_similarity(pt, w.B, model, gk)
+    ctx.device_status()
+    assert torch.equal(got, ref)
+    if groups <= 11:
+        H = O.hdc_encode(np.concatenate(Xs), Wt, w.shift, w.bits)
+        assert np.array_equal(_u32(ctx.decrypt_scores(sk, got, w.B)), O.clear_scores(H, cls))
+    ctx.close()

@@ -224,3 +224,29 @@ def test_face1024_full_size_bit_exact():
     out = c.ctx.infer(c.g_X, c.g_Wt, c.g_model, c.g_gk)
     assert torch.equal(out, c.g_out)
     c.ctx.close()
+
+
+@pytest.mark.slow
+def test_dense65536_full_size_sampled():
+    """65536 queries, F=1024, D=16384, 8-bit HVs, 16 classes, n=16384, 6 primes, layout
+    k_in=1 r=16 (64 groups, 4 rotations): sampled hypervector rows against the oracle's
+    projection and every sampled query's 16 decrypted scores against the clear dot
+    products mod t."""
+    w = WL.config("dense65536")
+    ctx = E.Context.for_workload(w)
+    X = WL.features(w.seed, w.B, w.F)
+    Wt = WL.projection(w.seed, w.D, w.F)
+    cls = WL.classes(w.seed, w.k, w.D)
+    sk, gk = ctx.keygen(w.seed)
+    model = ctx.encrypt_model(_dev(cls), sk, w.seed)
+    gX, gW = _dev(X), _dev(Wt)
+    H = ctx.hdc_encode(gX, gW)
+    out = ctx.infer(gX, gW, model, gk)
+    scores = _u32(ctx.decrypt_scores(sk, out, w.B))
+    ctx.device_status()
+    rng = np.random.default_rng(11)
+    rows = np.unique(np.concatenate([rng.integers(0, w.B, 192), [0, 1023, 1024, w.B - 1]]))
+    Ho = O.hdc_encode(X[rows], Wt, w.shift, w.bits)
+    assert np.array_equal(H.cpu().numpy()[rows], Ho)
+    assert np.array_equal(scores[rows], O.clear_scores(Ho, cls))
+    ctx.close()
