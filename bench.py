@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--no-perquery", action="store_true")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--mac-mode", type=int, default=-1,
+                    help="force the multiply-accumulate schedule (profiling)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
     return ap.parse_args()
@@ -207,6 +209,8 @@ def run_ours(args, w, B):
         from paper_2511_00737_gb300 import batching as BT
     # packed multi-client steps replay whole groups, so reserve full groups
     ctx = E.Context.for_workload(w, max_batch=(-(-B // cap) * cap) if multi else B)
+    if args.mac_mode >= 0:
+        ctx.tune_set("mac_mode", args.mac_mode)
     sk, gk = ctx.keygen(seed)
     cls = torch.from_numpy(WL.classes(seed, w.k, w.D)).to(dev)
     model = ctx.encrypt_model(cls, sk, seed)
@@ -219,7 +223,10 @@ def run_ours(args, w, B):
         Xd = [[x.to(dev) for x in xs] for xs in Xh]
         pipe = BT.GraphedPipeline(ctx, Wt, model, gk, max_groups=ctx.groups(B))
         pt0 = ctx.encode_plain(ctx.hdc_encode(torch.cat(Xd[0]), Wt))
-        tuned, tuned_ms, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=3)
+        if args.mac_mode >= 0:
+            tuned = {"mac_mode": args.mac_mode}
+        else:
+            tuned, tuned_ms, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=3)
         del pt0
         out = pipe.out
         step = lambda i: pipe.run(Xd[i % R])
