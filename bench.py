@@ -234,6 +234,13 @@ def run_ours(args, w, B):
         Xh = [torch.from_numpy(WL.features(seed, B, w.F, batch=b)).pin_memory() for b in range(R)]
         Xd = [x.to(dev) for x in Xh]
         out = ctx.out_ct(B)
+        tuned = None
+        if ctx.groups(B) >= 2 and args.mac_mode < 0:
+            # several groups share each model read: let the autotuner pick the schedule
+            from paper_2511_00737_gb300 import autotune as AT
+            pt0 = ctx.encode_plain(ctx.hdc_encode(Xd[0], Wt))
+            tuned, _, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=2)
+            del pt0
         step = lambda i: ctx.infer(Xd[i % R], Wt, model, gk, out=out)
     out_h = torch.empty(out.shape, dtype=out.dtype).pin_memory()
     torch.cuda.synchronize()
@@ -330,6 +337,8 @@ def run_ours(args, w, B):
                 "roofline": roof, "cpu_baseline": cpu,
                 "stages_ms_per_step": {k: v / max(1, args.steps) for k, v in stage_ms.items()},
                 "per_query_form": perq}
+        if not multi and tuned:
+            line["config"]["mac_schedule"] = tuned
         if multi:
             line["config"]["clients"] = len(w.clients)
             line["config"]["mac_schedule"] = tuned

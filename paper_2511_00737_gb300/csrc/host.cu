@@ -119,7 +119,9 @@ struct ephdc_ctx {
   // plaintext ranges), 2 = tiled multi-group
   int mac_mode = 0;
   int mac_min_groups = 4;  // automatic mode: tiled from this many groups on
-  int mac_tc_min_groups = 8;  // automatic mode: tensor cores from this many groups on
+  // automatic mode: tensor cores from this many groups on (off unless tuned: on this
+  // part the byte-split product does not yet beat the tiled CUDA-core kernel)
+  int mac_tc_min_groups = 1 << 30;
   int mac_splits = 0;      // streaming: split count cap (0 = heuristic)
   ephdc::MacTiling tile = {4, 8, 32, 8};
 };
@@ -509,7 +511,7 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
   const int G = (int)groups_for(c, B);
   cudaError_t e;
   {
-    const bool tc_ok = 2 * d.Kp <= 32;
+    const bool tc_ok = 2 * d.Kp <= 32 && d.P < 16384;
     const bool tc = tc_ok && (c->mac_mode == 3 ||
                               (c->mac_mode == 0 && G >= c->mac_tc_min_groups));
     const bool tiled = !tc && (c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups));

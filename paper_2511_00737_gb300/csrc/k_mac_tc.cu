@@ -8,8 +8,8 @@
 // rows (u, g) of the digit matrix A' (4 GP x K) times columns (v, o) of B' (K x 4 OP).
 // Bytes are fp16 values, products are < 2^16, and a window of 256 plaintexts keeps
 // every fp32 partial sum below 2^24: exact.  After each window the TMEM accumulator
-// is read out, recombined with 2^(8(u+v)) mod q_l and added to 64-bit shared
-// accumulators; the next window restarts the MMA accumulation.
+// is read out, each S_uv is multiplied by 2^(8(u+v)) mod q_l and added to 64-bit
+// shared accumulators (reduced once at the end); the next window restarts the MMA.
 //
 // One CTA: limb l, KB consecutive coefficients, one block of GP groups, all outputs.
 // Per 16-plaintext chunk: cp.async stages the raw residues (rows of KB words) into a
@@ -120,11 +120,14 @@ struct TcCfg {
   static constexpr int A_BYTES = 4 * GP * KC * 2;  // per coefficient
   static constexpr int B_BYTES = N * KC * 2;
   static constexpr int OPS_BYTES = KB * (A_BYTES + B_BYTES);  // one operand buffer
+  // operand buffers in flight (the MMAs of chunk c must finish before chunk c + NB
+  // reuses their buffer); deeper rings cost occupancy and measured slower
+  static constexpr int NB = 2;
   static constexpr int TCOLS = KB * MT * N;                   // TMEM columns
   static constexpr uint32_t IDESC =
       (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   static constexpr size_t SMEM =
-      1024 + 2 * OPS_BYTES + RING * RAW_WORDS * 4 + KB * GP * OP * 8 + 64;
+      1024 + NB * OPS_BYTES + RING * RAW_WORDS * 4 + KB * GP * OP * 8 + 128;
 };
 
 template <int MT, int OP, int KB>
@@ -136,11 +139,12 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
   constexpr int GP = C::GP, N = C::N, KC = C::KC;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* ops = sm;                                                // [2][KB][A | B]
-  uint32_t* raw = (uint32_t*)(sm + 2 * C::OPS_BYTES);               // [RING][ROWS][RSTRIDE]
-  unsigned long long* accs = (unsigned long long*)(raw + C::RING * C::RAW_WORDS);  // [KB][GP][OP]
+  uint8_t* ops = sm;                                                // [NB][KB][A | B]
+  uint32_t* raw = (uint32_t*)(sm + C::NB * C::OPS_BYTES);           // [RING][ROWS][RSTRIDE]
+  unsigned long long* accs = (unsigned long long*)(raw + C::RING * C::RAW_WORDS);  // [KB][OP][GP]
   uint64_t* bars = (uint64_t*)(accs + KB * GP * OP);                // MMA done, per buffer
-  uint32_t* tslot = (uint32_t*)(bars + 2);
+  uint32_t* tslot = (uint32_t*)(bars + 4);
+  uint32_t* Wsh = tslot + 2;                                        // 2^(8e) mod q_l, e < 7
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t l = blockIdx.y, k0 = blockIdx.x * KB;
@@ -152,8 +156,8 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
 
   for (int i = tid; i < KB * GP * OP; i += blockDim.x) accs[i] = 0;
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[1])));
+    for (int b = 0; b < C::NB; b++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&bars[b])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -169,24 +173,39 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
   const uint32_t tmem = *tslot;
 
   // raw residues of chunk ch: rows g (plaintexts of group g0 + g) and GP + o (model
-  // output o), each KC plaintexts x KB coefficients; zero outside the batch
+  // output o), each KC plaintexts x KB coefficients; zero outside the batch.  Every
+  // thread copies the same (row, plaintext-in-chunk) pieces in every chunk, so their
+  // chunk-0 sources and per-chunk strides are set up once.
+  constexpr int COPIES = (C::ROWS * KC + 255) / 256;
+  const uint32_t* csrc[COPIES];
+  size_t cstep[COPIES];
+  int cdst[COPIES], cii[COPIES];
+  bool crow[COPIES];
+#pragma unroll
+  for (int q = 0; q < COPIES; q++) {
+    const int t = tid + q * 256;
+    const int row = t / KC, ii = t - row * KC;
+    cii[q] = ii;
+    cdst[q] = t < C::ROWS * KC ? row * C::RSTRIDE + ii * KB : -1;
+    if (row < GP) {
+      const int g = g0 + row;
+      crow[q] = g < G;
+      csrc[q] = pt + (((size_t)(crow[q] ? g : 0) * P + ii) * L + l) * n + k0;
+      cstep[q] = (size_t)KC * L * n;
+    } else {
+      const int o = row - GP;
+      crow[q] = o < O;
+      csrc[q] = model + (((size_t)ii * O + (crow[q] ? o : 0)) * L + l) * n + k0;
+      cstep[q] = (size_t)KC * O * L * n;
+    }
+  }
   auto load_raw = [&](int ch, int stage) {
     uint32_t* dst = raw + stage * C::RAW_WORDS;
-    for (int t = tid; t < C::ROWS * KC; t += blockDim.x) {
-      const int row = t / KC, ii = t - row * KC;
-      const uint32_t i = (uint32_t)ch * KC + ii;
-      bool ok = i < P;
-      const uint32_t* src;
-      if (row < GP) {
-        const int g = g0 + row;
-        ok = ok && g < G;
-        src = pt + (((size_t)(ok ? g : 0) * P + (ok ? i : 0)) * L + l) * n + k0;
-      } else {
-        const int o = row - GP;
-        ok = ok && o < O;
-        src = model + (((size_t)(ok ? i : 0) * O + (ok ? o : 0)) * L + l) * n + k0;
-      }
-      cp_async<KB * 4>(dst + row * C::RSTRIDE + ii * KB, src, ok);
+#pragma unroll
+    for (int q = 0; q < COPIES; q++) {
+      if (cdst[q] < 0) continue;
+      const bool ok = crow[q] && (uint32_t)(ch * KC + cii[q]) < P;
+      cp_async<KB * 4>(dst + cdst[q], ok ? csrc[q] + (size_t)ch * cstep[q] : csrc[q], ok);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
@@ -205,10 +224,14 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
       const int ii = cc * 8 + 2 * kp;              // K pair (ii, ii + 1)
       const uint32_t* w = rs + (isA ? rr : GP + rr) * C::RSTRIDE + ii * KB;
       uint32_t x[KB], y[KB];
-#pragma unroll
-      for (int j = 0; j < KB; j++) {
-        x[j] = w[j];
-        y[j] = w[KB + j];
+      if (KB == 4) {
+        const uint4 a = *reinterpret_cast<const uint4*>(w);
+        const uint4 b = *reinterpret_cast<const uint4*>(w + 4);
+        x[0] = a.x; x[1 % KB] = a.y; x[2 % KB] = a.z; x[3 % KB] = a.w;
+        y[0] = b.x; y[1 % KB] = b.y; y[2 % KB] = b.z; y[3 % KB] = b.w;
+      } else {
+        const uint4 a = *reinterpret_cast<const uint4*>(w);  // (x0, x1, y0, y1)
+        x[0] = a.x; x[1 % KB] = a.y; y[0] = a.z; y[1 % KB] = a.w;
       }
 #pragma unroll
       for (int j = 0; j < KB; j++) {
@@ -222,10 +245,11 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
     }
   };
 
-  uint32_t W[7];  // 2^(8e) mod q_l
-  W[0] = 1;
-#pragma unroll
-  for (int e = 1; e < 7; e++) W[e] = mulm(W[e - 1], 256u, m);
+  if (tid == 0) {
+    uint32_t w = 1;
+    for (int e = 0; e < 7; e++, w = mulm(w, 256u, m)) Wsh[e] = w;
+  }
+  const uint32_t accs_s = smem_u32(accs);
 
   for (int s = 0; s < C::RING - 1; s++) {
     if (s < nch) load_raw(s, s);
@@ -233,7 +257,7 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
   }
   bool alive = true;
   for (int ch = 0; ch < nch; ch++) {
-    const int buf = ch & 1;
+    const int buf = ch % C::NB;
     asm volatile("cp.async.wait_group %0;\n" ::"n"(C::RING - 2) : "memory");
     __syncthreads();
     {
@@ -241,11 +265,15 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
       if (nx < nch) load_raw(nx, nx % C::RING);
       else asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    bool ok = true;
-    if (ch >= 2) ok = mbar_wait(smem_u32(&bars[buf]), ((ch - 2) >> 1) & 1, status, 11);
-    if (ok && alive) transform(ch % C::RING, buf);
+    if (ch >= C::NB) {  // operand buffer `buf` was read by the MMAs of chunk ch - NB
+      bool ok = true;
+      if (tid == 0)
+        ok = mbar_wait(smem_u32(&bars[buf]), ((ch - C::NB) / C::NB) & 1, status, 11);
+      alive = __syncthreads_and(alive && ok);
+    }
+    if (alive) transform(ch % C::RING, buf);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    alive = __syncthreads_and(alive && ok);
+    __syncthreads();
     if (tid == 0 && alive) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       const uint32_t ob = smem_u32(ops + buf * C::OPS_BYTES);
@@ -262,8 +290,9 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
     }
     if ((ch % C::WIN) == C::WIN - 1 || ch == nch - 1) {
       // window complete: every S_uv of these 256 plaintexts is in TMEM
-      ok = alive && mbar_wait(smem_u32(&bars[buf]), (ch >> 1) & 1, status, 12);
-      alive = __syncthreads_and(ok);
+      bool ok = true;
+      if (tid == 0) ok = alive && mbar_wait(smem_u32(&bars[buf]), (ch / C::NB) & 1, status, 12);
+      alive = __syncthreads_and(alive && ok);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       if (alive) {
         const int q = warp & 3, h = warp >> 2;
@@ -284,9 +313,14 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
                 for (int e = 0; e < 32; e++) {
                   const int col = col0 + e, vv = col / OP, o = col - vv * OP;
                   if (o < O) {
-                    const uint32_t s = (uint32_t)__float2uint_rz(__uint_as_float(v[e]));
-                    atomicAdd(&accs[(j * GP + g) * OP + o],
-                              (unsigned long long)mulm(s, W[u + vv], m));
+                    // S_uv < 2^24 and 2^(8(u+v)) mod q < 2^30: products < 2^54, at most
+                    // 16 per window and 63 windows (P < 16384) stay below 2^64
+                    const uint32_t sv = (uint32_t)__float2uint_rz(__uint_as_float(v[e]));
+                    const uint64_t add = (uint64_t)sv * Wsh[u + vv];
+                    asm volatile("red.shared.add.u64 [%0], %1;\n" ::"r"(
+                                     accs_s + 8u * (uint32_t)((j * OP + o) * GP + g)),
+                                 "l"(add)
+                                 : "memory");
                   }
                 }
               }
@@ -303,7 +337,7 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
     const int o = rest % OP, g = rest / OP;
     if (g0 + g < G && o < O)
       out[(((size_t)(g0 + g) * O + o) * L + l) * n + k0 + j] =
-          red64(accs[(j * GP + g) * OP + o], m.p, m.mu);
+          red64(accs[(j * OP + o) * GP + g], m.p, m.mu);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
