@@ -444,6 +444,16 @@ def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
     P, Kp, L, n = ctx.P, ctx.Kp, ctx.L, ctx.n
     calls = max(1, stage_calls[dom])
     t = stage_ms[dom] / calls / 1000.0
+    if dom == "mac" and G >= 2:
+        # several groups per model read: a compute-bound multi-group contraction
+        macs = G * P * 2 * Kp * L * n
+        ach = macs / t / 1e12
+        peak = 152 * 64 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 2 / 1e12
+        return {"kernel": "ptct_mac (multi-group, %d groups)" % G, "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "Tmodmac/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "derived: 152 SMs x 64 IMAD lanes x clock / "
+                                                 "2 instructions per 64-bit multiply-add",
+                "ms_per_launch": t * 1000.0}
     if dom == "mac":
         model = P * Kp * 2 * L * n * 4
         pt = G * P * L * n * 4
