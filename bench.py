@@ -231,18 +231,23 @@ def run_ours(args, w, B):
             tuned, tuned_ms, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=3)
         del pt0
         out = pipe.out
+        enc, _, _ = AT.tune_encode(ctx, ctx.hdc_encode(torch.cat(Xd[0]), Wt), reps=3)
+        tuned = {**tuned, **enc}
         step = lambda i: pipe.run(Xd[i % R])
     else:
         Xh = [torch.from_numpy(WL.features(seed, B, w.F, batch=b)).pin_memory() for b in range(R)]
         Xd = [x.to(dev) for x in Xh]
         out = ctx.out_ct(B)
-        tuned = None
+        from paper_2511_00737_gb300 import autotune as AT
+        H0 = ctx.hdc_encode(Xd[0], Wt)
+        tuned, _, _ = AT.tune_encode(ctx, H0, reps=5)  # pass schedule of the transforms
         if ctx.groups(B) >= 2 and args.mac_mode < 0:
             # several groups share each model read: let the autotuner pick the schedule
-            from paper_2511_00737_gb300 import autotune as AT
-            pt0 = ctx.encode_plain(ctx.hdc_encode(Xd[0], Wt))
-            tuned, _, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=2)
+            pt0 = ctx.encode_plain(H0)
+            mac, _, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=2)
+            tuned = {**tuned, **mac}
             del pt0
+        del H0
         # consecutive batches alternate over S streams, each with its own context
         # (scratch) and output, sharing the resident model and keys, so one batch's
         # latency-bound rotations overlap the next batch's encoding and MAC

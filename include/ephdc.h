@@ -195,7 +195,9 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* ctx, const ephdc_request* reqs, int32_
  * byte split, k/k_in <= 16), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
  * cores from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
  * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
- * warp, groups per CTA, plaintexts per staged chunk, at most 15).  EPHDC_EINVAL for an unknown
+ * warp, groups per CTA, plaintexts per staged chunk, at most 15); "ntt_plan" 0/1/2
+ * is the pass schedule of the encoding transforms (balanced, radix-32 passes first,
+ * radix-32 passes last).  EPHDC_EINVAL for an unknown
  * knob or an invalid value.  ephdc_tune_get returns -1 for an unknown knob. */
 ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);
 int64_t ephdc_tune_get(const ephdc_ctx* ctx, const char* knob);

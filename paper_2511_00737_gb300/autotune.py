@@ -100,3 +100,26 @@ def tune_similarity(ctx, pt, B, model, gk, reps=5, use_cache=True, max_candidate
         cache[key] = {"knobs": best, "ms": best_ms}
         _save(cache)
     return best, best_ms, table
+
+
+def tune_encode(ctx, H, reps=5, use_cache=True):
+    """Pick the fastest pass schedule of the encoding transforms for this batch."""
+    B = H.shape[0]
+    key = _key(ctx, ctx.groups(B)) + "|encode"
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        apply(ctx, cache[key]["knobs"])
+        return cache[key]["knobs"], cache[key]["ms"], []
+    table = []
+    for v in (0, 1, 2):
+        ctx.tune_set("ntt_plan", v)
+        ms = _time(lambda: ctx.encode_plain(H), reps)
+        table.append((ms, {"ntt_plan": v}))
+    table.sort(key=lambda x: x[0])
+    best_ms, best = table[0]
+    apply(ctx, best)
+    if use_cache:
+        cache = _load()
+        cache[key] = {"knobs": best, "ms": best_ms}
+        _save(cache)
+    return best, best_ms, table

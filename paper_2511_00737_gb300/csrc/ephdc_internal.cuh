@@ -49,6 +49,7 @@ struct DevCtx {
   uint16_t* xh;              // [max_batch][F] fp16 features
   uint16_t* wh;              // [D][F] fp16 projection
   uint32_t* status;          // nonzero when a bounded device wait gave up
+  int32_t ntt_plan;          // pass schedule of the encoding transforms (NttPlan V)
   uint64_t cdt[EPHDC_CDT_LEN];
 };
 
@@ -234,14 +235,21 @@ static __device__ __noinline__ void ntt_inv_smem(uint32_t* s, uint32_t logn, con
 // and shared-memory offset is a constant, each element costs one shared load and one
 // shared store per pass, and the final reduction (forward) or n^-1 scaling (inverse)
 // is folded into the last pass.
-template <int LOGN>
+// Pass schedules (the "radix" choice): the last pass always has K = min(5, log n)
+// contiguous elements; the other log n - 5 stages are split into passes of at most 5
+// stages.  V = 0: balanced split; V = 1: radix-32 passes first; V = 2: radix-32
+// passes last.  Every split keeps the non-contiguous strides >= 32.
+template <int LOGN, int V = 0>
 struct NttPlan {
   static constexpr int LAST = LOGN < 5 ? LOGN : 5;
   static constexpr int REST = LOGN - LAST;
   static constexpr int FRONT = (REST + 4) / 5;
   static constexpr int NP = FRONT + 1;
   __host__ __device__ static constexpr int K(int i) {
-    return i == FRONT ? LAST : (REST / FRONT + (i < REST % FRONT ? 1 : 0));
+    return i == FRONT ? LAST
+         : V == 1     ? (i < REST / 5 ? 5 : REST - 5 * (REST / 5))
+         : V == 2     ? (i == 0 && REST % 5 ? REST % 5 : 5)
+                      : (REST / FRONT + (i < REST % FRONT ? 1 : 0));
   }
   __host__ __device__ static constexpr int LOGM0(int i) {
     int s = 0;
@@ -337,9 +345,9 @@ __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP&
   }
 }
 
-template <int LOGN, int I, class LD, class ST>
+template <int LOGN, int I, class LD, class ST, int V = 0>
 __device__ __forceinline__ void fwd_passes(uint32_t* s, const ModP& m, LD ld, ST st) {
-  using Pl = NttPlan<LOGN>;
+  using Pl = NttPlan<LOGN, V>;
   if constexpr (I < Pl::NP) {
     constexpr bool first = I == 0, last = I == Pl::NP - 1;
     if constexpr (first && last) {
@@ -352,12 +360,12 @@ __device__ __forceinline__ void fwd_passes(uint32_t* s, const ModP& m, LD ld, ST
       pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), true, false>(m.tw, m, SmemLd{s}, SmemSt{s});
     }
     __syncthreads();
-    fwd_passes<LOGN, I + 1>(s, m, ld, st);
+    fwd_passes<LOGN, I + 1, LD, ST, V>(s, m, ld, st);
   }
 }
-template <int LOGN, int I, class LD, class ST>
+template <int LOGN, int I, class LD, class ST, int V = 0>
 __device__ __forceinline__ void inv_passes(uint32_t* s, const ModP& m, LD ld, ST st) {
-  using Pl = NttPlan<LOGN>;
+  using Pl = NttPlan<LOGN, V>;
   if constexpr (I >= 0) {
     constexpr bool first = I == Pl::NP - 1, last = I == 0;
     if constexpr (first && last) {
@@ -370,30 +378,30 @@ __device__ __forceinline__ void inv_passes(uint32_t* s, const ModP& m, LD ld, ST
       pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, SmemLd{s}, SmemSt{s});
     }
     __syncthreads();
-    inv_passes<LOGN, I - 1>(s, m, ld, st);
+    inv_passes<LOGN, I - 1, LD, ST, V>(s, m, ld, st);
   }
 }
 // Forward NTT: `ld(i)` supplies natural-order input i (values in [0, 4p)) to the first
 // pass, `st(j, v)` receives device-order output j (in [0, p)) from the last pass;
 // shared buffer `s` (padded) carries the passes in between.  Ends with a barrier.
-template <int LOGN, class LD, class ST>
+template <int LOGN, class LD, class ST, int V = 0>
 __device__ __forceinline__ void ntt_fwd_io(uint32_t* s, const ModP& m, LD ld, ST st) {
-  fwd_passes<LOGN, 0>(s, m, ld, st);
+  fwd_passes<LOGN, 0, LD, ST, V>(s, m, ld, st);
 }
 // Inverse NTT: device-order input (values in [0, 2p)) in, natural-order output in
 // [0, p) out.  Ends with a barrier.
-template <int LOGN, class LD, class ST>
+template <int LOGN, class LD, class ST, int V = 0>
 __device__ __forceinline__ void ntt_inv_io(uint32_t* s, const ModP& m, LD ld, ST st) {
-  inv_passes<LOGN, NttPlan<LOGN>::NP - 1>(s, m, ld, st);
+  inv_passes<LOGN, NttPlan<LOGN, V>::NP - 1, LD, ST, V>(s, m, ld, st);
 }
 // in-place variants on the padded shared buffer
-template <int LOGN>
+template <int LOGN, int V = 0>
 __device__ __forceinline__ void ntt_fwd_t(uint32_t* s, const ModP& m) {
-  ntt_fwd_io<LOGN>(s, m, SmemLd{s}, SmemSt{s});
+  ntt_fwd_io<LOGN, SmemLd, SmemSt, V>(s, m, SmemLd{s}, SmemSt{s});
 }
-template <int LOGN>
+template <int LOGN, int V = 0>
 __device__ __forceinline__ void ntt_inv_t(uint32_t* s, const ModP& m) {
-  ntt_inv_io<LOGN>(s, m, SmemLd{s}, SmemSt{s});
+  ntt_inv_io<LOGN, SmemLd, SmemSt, V>(s, m, SmemLd{s}, SmemSt{s});
 }
 
 // dispatch a kernel template on log2(n) (n = 1024 .. 16384)

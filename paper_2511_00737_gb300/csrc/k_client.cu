@@ -30,9 +30,9 @@ __device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t 
 // positions through the context's scatter table; then the inverse NTT mod t gives the
 // plaintext coefficients, and for each limb the centred lift feeds the forward NTT,
 // whose output is staged in shared memory and stored with 16-byte writes.
-template <int LOGN>
-__global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3) k_encode_plain(DevCtx c, const int8_t* __restrict__ H,
-                                                      int B, uint32_t* __restrict__ pt) {
+template <int LOGN, int V>
+__global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
+    k_encode_plain(DevCtx c, const int8_t* __restrict__ H, int B, uint32_t* __restrict__ pt) {
   constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   uint32_t* mb = sm;
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3) k_
     for (uint32_t jin = 0; jin < kin; jin++) mb[padi(__ldg(&sc[jin]))] = v;
   }
   __syncthreads();
-  ntt_inv_t<LOGN>(mb, c.mt);  // slots -> coefficients in [0, t)
+  ntt_inv_t<LOGN, V>(mb, c.mt);  // slots -> coefficients in [0, t)
   constexpr uint32_t thalf = (EPHDC_T - 1) / 2;
   for (uint32_t l = 0; l < c.L; l++) {
     const uint32_t p = c.mq[l].p;
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3) k_
       const uint32_t v = mb[padi(k)];
       return v <= thalf ? v : v + p - EPHDC_T;  // centred lift into Z_{q_l}
     };
-    ntt_fwd_io<LOGN>(wb, c.mq[l], lift, SmemSt{wb});
+    ntt_fwd_io<LOGN, decltype(lift), SmemSt, V>(wb, c.mq[l], lift, SmemSt{wb});
     uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
     for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
       dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
@@ -374,9 +374,11 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
   const int G = (B + c.cap - 1) / c.cap;
   const size_t smem = 2 * padded_words(c.n) * sizeof(uint32_t);
   EPHDC_DISPATCH_LOGN(c.logn, LG, {
-    cudaError_t e = set_smem(k_encode_plain<LG>, smem);
+    auto kern = c.ntt_plan == 1 ? k_encode_plain<LG, 1>
+              : c.ntt_plan == 2 ? k_encode_plain<LG, 2> : k_encode_plain<LG, 0>;
+    cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    k_encode_plain<LG><<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
+    kern<<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
   });
   return cudaGetLastError();
 }

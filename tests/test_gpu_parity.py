@@ -250,3 +250,27 @@ def test_dense65536_full_size_sampled():
     assert np.array_equal(H.cpu().numpy()[rows], Ho)
     assert np.array_equal(scores[rows], O.clear_scores(Ho, cls))
     ctx.close()
+
+
+@pytest.mark.parametrize("n,L,r", [(2048, 2, 2), (4096, 3, 8), (8192, 4, 8), (16384, 6, 16)])
+def test_every_ntt_plan_gives_the_same_plaintexts(n, L, r):
+    """The pass schedules of the encoding transforms differ only in speed."""
+    w = WL.Workload(name="t", n=n, L=L, k=2, k_in=1, r=r, D=96, F=32, bits=8, B=300, seed=n)
+    ctx = E.Context.for_workload(w)
+    X = WL.features(w.seed, w.B, w.F)
+    Wt = WL.projection(w.seed, w.D, w.F)
+    H = ctx.hdc_encode(_dev(X), _dev(Wt))
+    ref = None
+    for v in (0, 1, 2):
+        ctx.tune_set("ntt_plan", v)
+        pt = ctx.encode_plain(H)
+        if ref is None:
+            ref = pt
+            o = O.Oracle(w.n, w.L, w.k, w.k_in, w.r, w.D)
+            m = o.encode_plain(O.hdc_encode(X, Wt, w.shift, w.bits))
+            G = o.groups(w.B)
+            got = ctx.plain_to_host_coeff(pt, G * o.P)
+            assert np.array_equal(got, _lifted(m.reshape(G * o.P, n), o.q))
+        else:
+            assert torch.equal(pt, ref), v
+    ctx.close()
