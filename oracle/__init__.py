@@ -68,6 +68,9 @@ def lib():
             "or_decrypt_slots": (None, [vp, vp, vp, vp]),
             "or_encrypt_slots": (None, [vp, u64, u64, vp, vp, vp]),
             "or_noise_budget": (dbl, [vp, vp, vp]),
+            "or_encrypt_queries": (None, [vp, u64, vp, i32, vp, vp]),
+            "or_encode_model_plain": (None, [vp, vp, vp]),
+            "or_ctpt_mac": (None, [vp, vp, i32, vp, vp]),
             "or_num_threads": (ctypes.c_int, []),
             "or_set_threads": (None, [ctypes.c_int]),
         }
@@ -312,6 +315,26 @@ class Oracle:
         acc = self.ptct_mac(m, H.shape[0], model)
         out = self.rotate_sum(gk, acc)
         return H, m, out
+
+    # server-side variant (HE-HDC-SR, Sec. 3) -----------------------------------
+    def encrypt_queries(self, seed, H, s):
+        """Client side of the server-side method: every query plaintext encrypted."""
+        H = np.ascontiguousarray(H, np.int8)
+        B = H.shape[0]
+        ctq = np.zeros((self.groups(B), self.P, 2, self.L, self.n), np.uint32)
+        lib().or_encrypt_queries(self.ctx, seed, _p(H), B, _p(np.ascontiguousarray(s, np.int32)),
+                                 _p(ctq))
+        return ctq
+
+    def encode_model_plain(self, classes):
+        mm = np.zeros((self.Kp, self.P, self.n), np.uint32)
+        lib().or_encode_model_plain(self.ctx, _p(np.ascontiguousarray(classes, np.int8)), _p(mm))
+        return mm
+
+    def ctpt_mac(self, ctq, B, mm):
+        acc = np.zeros((self.groups(B), self.Kp, 2, self.L, self.n), np.uint32)
+        lib().or_ctpt_mac(self.ctx, _p(_u32(ctq)), B, _p(_u32(mm)), _p(acc))
+        return acc
 
     # server check ------------------------------------------------------------
     def decrypt(self, s, ct):

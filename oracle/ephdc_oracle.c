@@ -939,3 +939,91 @@ void or_set_threads(int k) { if (k > 0) omp_set_num_threads(k); }
 int or_num_threads(void) { return 1; }
 void or_set_threads(int k) { (void)k; }
 #endif
+
+/* ------------------------------------------------------------------------- */
+/* Server-side variant (HE-HDC-SR, Sec. 3): the client encrypts its queries    */
+/* ------------------------------------------------------------------------- */
+/* Query plaintext (g, i) encrypted with the secret key: c1 = a (domain 6),
+ * c0 = -a s + e (domain 7) + Delta m, obj = g*P + i.  ctq: [G][P][2][L][n]. */
+void or_encrypt_queries(const or_ctx* c, u64 seed, const int8_t* H, i32 B, const i32* s,
+                        u32* ctq) {
+  u32 n = c->n, L = c->L;
+  u32 G = (u32)((B + c->cap - 1) / c->cap);
+#pragma omp parallel
+  {
+    u32* slots = (u32*)malloc(sizeof(u32) * n);
+    u32* m = (u32*)malloc(sizeof(u32) * n);
+    u32* a = (u32*)malloc(sizeof(u32) * L * n);
+    i32* e = (i32*)malloc(sizeof(i32) * n);
+    u32* sl = (u32*)malloc(sizeof(u32) * n);
+    u32* as = (u32*)malloc(sizeof(u32) * n);
+#pragma omp for schedule(dynamic)
+    for (i64 gi = 0; gi < (i64)G * c->P; gi++) {
+      u32 g = (u32)(gi / c->P), i = (u32)(gi % c->P);
+      query_slots(c, H, B, g, i, slots);
+      or_slot_encode(n, c->t, c->zeta, slots, m);
+      or_sample_uniform(seed, 6, (u64)gi, n, L, c->q, a);
+      or_sample_gauss(seed, 7, (u64)gi, n, c->cdt, e);
+      for (u32 l = 0; l < L; l++) {
+        u32 p = c->q[l];
+        for (u32 kk = 0; kk < n; kk++) sl[kk] = smod(s[kk], p);
+        or_polymul(n, p, c->psi[l], a + (u64)l * n, sl, as);
+        u32* c0 = ctq + (((u64)gi * 2 + 0) * L + l) * n;
+        u32* c1 = ctq + (((u64)gi * 2 + 1) * L + l) * n;
+        for (u32 kk = 0; kk < n; kk++) {
+          u32 v = submod(smod(e[kk], p), as[kk], p);
+          c0[kk] = addmod(v, mulmod(c->delta[l], m[kk], p), p);
+          c1[kk] = a[(u64)l * n + kk];
+        }
+      }
+    }
+    free(slots); free(m); free(a); free(e); free(sl); free(as);
+  }
+}
+
+/* Model plaintexts of the server-side variant: mm[jp][i] = encode(class slots of
+ * ciphertext (i, jp)) mod t, coefficient domain.  mm: [Kp][P][n]. */
+void or_encode_model_plain(const or_ctx* c, const int8_t* classes, u32* mm) {
+  u32 n = c->n;
+#pragma omp parallel
+  {
+    u32* slots = (u32*)malloc(sizeof(u32) * n);
+#pragma omp for schedule(dynamic)
+    for (i64 ji = 0; ji < (i64)c->Kp * c->P; ji++) {
+      u32 jp = (u32)(ji / c->P), i = (u32)(ji % c->P);
+      class_slots(c, classes, i, jp, slots);
+      or_slot_encode(n, c->t, c->zeta, slots, mm + (u64)ji * n);
+    }
+    free(slots);
+  }
+}
+
+/* Server computation: acc[g][jp][poly][l] = sum_i ctq[g][i][poly][l] * lift(mm[jp][i]). */
+void or_ctpt_mac(const or_ctx* c, const u32* ctq, i32 B, const u32* mm, u32* acc) {
+  u32 n = c->n, L = c->L;
+  u32 G = (u32)((B + c->cap - 1) / c->cap);
+  i64 jobs = (i64)G * c->Kp * 2 * L;
+#pragma omp parallel
+  {
+    u32* lm = (u32*)malloc(sizeof(u32) * n);
+    u32* prod = (u32*)malloc(sizeof(u32) * n);
+#pragma omp for schedule(dynamic)
+    for (i64 job = 0; job < jobs; job++) {
+      u32 l = (u32)(job % L);
+      u32 poly = (u32)((job / L) % 2);
+      u32 jp = (u32)((job / (2 * L)) % c->Kp);
+      u32 g = (u32)(job / (2 * L * c->Kp));
+      u32 p = c->q[l];
+      u32* out = acc + ((((u64)g * c->Kp + jp) * 2 + poly) * L + l) * n;
+      for (u32 kk = 0; kk < n; kk++) out[kk] = 0;
+      for (u32 i = 0; i < c->P; i++) {
+        const u32* mi = mm + ((u64)jp * c->P + i) * n;
+        for (u32 kk = 0; kk < n; kk++) lm[kk] = lift(mi[kk], c->t, p);
+        const u32* ct = ctq + ((((u64)g * c->P + i) * 2 + poly) * L + l) * n;
+        or_polymul(n, p, c->psi[l], ct, lm, prod);
+        for (u32 kk = 0; kk < n; kk++) out[kk] = addmod(out[kk], prod[kk], p);
+      }
+    }
+    free(lm); free(prod);
+  }
+}
