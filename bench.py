@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--workload", default="face1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-perquery", action="store_true")
+    ap.add_argument("--no-sr", action="store_true",
+                    help="skip the client-runtime comparison with the server-side variant")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--streams", type=int, default=3,
@@ -382,6 +384,11 @@ def run_ours(args, w, B):
     if not args.no_perquery and rank == 0 and not multi:
         perq = per_query_form(w, dev)
 
+    # client runtime against the server-side variant, on one batch of at most 4 groups
+    clrt = None
+    if not args.no_sr and rank == 0 and not multi:
+        clrt = client_runtime(w, dev, min(B, 4 * cap))
+
     # roofline of the dominant stage
     pk, src = peaks()
     dom = max(stage_ms, key=lambda s: stage_ms[s])
@@ -400,7 +407,7 @@ def run_ours(args, w, B):
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "roofline": roof, "cpu_baseline": cpu,
                 "stages_ms_per_step": {k: v / max(1, args.steps) for k, v in stage_ms.items()},
-                "per_query_form": perq}
+                "per_query_form": perq, "client_runtime_vs_server_side": clrt}
         if not multi:
             line["config"]["streams"] = S
         if not multi and tuned:
@@ -414,6 +421,61 @@ def run_ours(args, w, B):
         cx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def client_runtime(w, dev, B, reps=5):
+    """Client cost of the client-side path vs the server-side variant (HE-HDC-SR) on
+    one batch of the workload (Sec. 6, Table t:clientrt): EP-HDC's client encodes
+    plaintexts and runs the HE compute; the HE-HDC-SR client encrypts its query
+    plaintexts and decrypts the returned scores.  HDC encoding, common to both, is
+    left out as in the paper's table.  Device milliseconds per batch, CUDA events on
+    one stream, after a warm-up."""
+    import torch
+    from paper_2511_00737_gb300 import ephdc as E
+    from paper_2511_00737_gb300 import workload as WL
+    ctx = E.Context.for_workload(w, max_batch=B)
+    sk, gk = ctx.keygen(w.seed)
+    cls = torch.from_numpy(WL.classes(w.seed, w.k, w.D)).to(dev)
+    model = ctx.encrypt_model(cls, sk, w.seed)
+    mm = ctx.encode_model_plain(cls)
+    Wt = torch.from_numpy(WL.projection(w.seed, w.D, w.F)).to(dev)
+    H = ctx.hdc_encode(torch.from_numpy(WL.features(w.seed, B, w.F)).to(dev), Wt)
+    pt = ctx.encode_plain(H)
+    ctq = ctx.encrypt_queries(H, sk, w.seed)
+    out = ctx.out_ct(B)
+    out_sr = ctx.out_ct(B)
+    scores = torch.empty((B, w.k), dtype=torch.int32, device=dev)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    encpt = timed(lambda: E.bfv_encode_plain(ctx.ctx, H, B, pt))
+    he = timed(lambda: E.bfv_ptct_similarity(ctx.ctx, pt, B, model, gk, out))
+    enc = timed(lambda: E.bfv_encrypt_queries(ctx.ctx, H, B, sk, w.seed, ctq))
+    srv = timed(lambda: E.bfv_ctpt_similarity(ctx.ctx, ctq, B, mm, gk, out_sr))
+    dec = timed(lambda: E.bfv_decrypt_scores(ctx.ctx, sk, out_sr, B, scores))
+    same = bool(torch.equal(ctx.decrypt_scores(sk, out, B), ctx.decrypt_scores(sk, out_sr, B)))
+    ctx.device_status()
+    up = int(E.lib().ephdc_query_ct_bytes(ctx.ctx, B))
+    down = int(E.lib().ephdc_out_ct_bytes(ctx.ctx, B))
+    ctx.close()
+    ep_ms, sr_ms = encpt + he, enc + dec
+    return {"batch": B, "unit": "ms per batch",
+            "client_side": {"client_ms": ep_ms, "encpt_ms": encpt, "he_compute_ms": he,
+                            "message_bytes": down},
+            "server_side": {"client_ms": sr_ms, "encrypt_ms": enc, "decrypt_ms": dec,
+                            "server_ms": srv, "upload_bytes": up, "download_bytes": down},
+            "client_speedup": sr_ms / ep_ms, "message_ratio": up / down,
+            "same_scores": same}
 
 
 def per_query_form(w, dev, queries=32):

@@ -190,6 +190,39 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* ctx, const ephdc_request* reqs, int32_
                                const int8_t* Wt_dev, const void* model_dev, const void* gk_dev,
                                uint32_t* out_ct_dev, void* stream);
 
+/* ---------------------------------------------------------------- server-side variant */
+/* HE-HDC-SR (Sec. 3, the comparison of Sec. 6, Table t:clientrt): the roles of the
+ * client-side path swapped.  The CLIENT holds the secret key and encrypts its query
+ * hypervectors in the SIMD form (one ciphertext per query plaintext, G*P of them per
+ * batch); the SERVER holds the class hypervectors as plaintexts, computes the same
+ * dot products ct x pt, rotates-and-sums, and returns G*(k/k_in) score ciphertexts
+ * that the client decrypts with bfv_decrypt_scores.  Same parameters, slot layout,
+ * Galois keys and output format as the client-side path. */
+size_t ephdc_query_ct_bytes(const ephdc_ctx* ctx, int32_t B); /* G*P ciphertexts        */
+size_t ephdc_model_plain_bytes(const ephdc_ctx* ctx);         /* (k/k_in)*P plaintexts  */
+
+/* Client: secret-key encryption of query plaintext (g, i) (its slots as in
+ * bfv_encode_plain): c1 = a, c0 = -a s + e + floor(q/t) m.  Randomness: ChaCha20
+ * keyed by the seed, ciphertext number g*P + i, domain 6 (a) and 7 (e).
+ * H_dev: int8 [B][D], 1 <= B <= max_batch.  query_ct_dev: ephdc_query_ct_bytes(B),
+ * [G][P][2][L][n] in the device NTT order (ephdc_ct_to_host_coeff reads it).
+ * Caller-owned, 16-byte aligned; EPHDC_EINVAL / EPHDC_ENOMEM as bfv_encode_plain. */
+ephdc_status bfv_encrypt_queries(ephdc_ctx* ctx, const int8_t* H_dev, int32_t B,
+                                 const void* sk_dev, uint64_t seed, uint32_t* query_ct_dev,
+                                 void* stream);
+/* Server (setup): class hypervector (jp*k_in + jin) as plaintexts mm[jp][i] holding
+ * c[i*r + ch] in slot (rho, ch*W + jin*cap_row + qq) for every qq < cap_row.
+ * class_hv_dev: int8 [k][D].  model_plain_dev: ephdc_model_plain_bytes(),
+ * [k/k_in][P][L][n] in the device NTT order (ephdc_plain_to_host_coeff reads it). */
+ephdc_status bfv_encode_model_plain(ephdc_ctx* ctx, const int8_t* class_hv_dev,
+                                    uint32_t* model_plain_dev, void* stream);
+/* Server: Acc[g][jp] = sum_i query_ct[g][i] * mm[jp][i] (negacyclic, per limb), then
+ * the rotate-and-sum and the export of ephdc_infer.  out_ct_dev:
+ * ephdc_out_ct_bytes(B), coefficient domain.  Uses the context's scratch. */
+ephdc_status bfv_ctpt_similarity(ephdc_ctx* ctx, const uint32_t* query_ct_dev, int32_t B,
+                                 const uint32_t* model_plain_dev, const void* gk_dev,
+                                 uint32_t* out_ct_dev, void* stream);
+
 /* Schedule knobs of the multi-accumulate (set by the autotuner; results never
  * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled / 3 tensor cores (exact
  * byte split, k/k_in <= 16), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
@@ -239,7 +272,8 @@ enum {
   EPHDC_STAGE_MAC = 2,     /* pt x ct multiply-accumulate (+ split reduce) */
   EPHDC_STAGE_ROTATE = 3,  /* rotate-and-sum with key switching            */
   EPHDC_STAGE_EXPORT = 4,  /* inverse NTT of the score ciphertexts         */
-  EPHDC_NSTAGES = 5
+  EPHDC_STAGE_ENCRYPT = 5, /* bfv_encrypt_queries (server-side variant)    */
+  EPHDC_NSTAGES = 6
 };
 /* When on, every client-path call records a CUDA event pair around each stage on the
  * call's own stream (no synchronisation).  Off by default. */

@@ -445,6 +445,73 @@ __device__ __forceinline__ void chacha_block(uint64_t seed, uint32_t domain, uin
   out[15] = x15 + in[15];
 }
 
+// ------------------------------------------------------------------ samplers
+// Gaussian coefficient from one 64-bit word: -19 + #{m : u >= cdt[m]}
+__device__ __forceinline__ int32_t cdt_sample(const DevCtx& c, uint64_t u) {
+  int32_t cnt = 0;
+#pragma unroll
+  for (int m = 0; m < EPHDC_CDT_LEN; m++) cnt += u >= c.cdt[m];
+  return cnt - 19;
+}
+
+// buf[padi(k)] = uniform coefficient k of limb l: 64-bit word l*n + k mod q_l
+__device__ __forceinline__ void fill_uniform(const DevCtx& c, uint64_t seed, uint32_t dom,
+                                             uint64_t obj, uint32_t l, uint32_t* buf) {
+  const uint32_t p = c.mq[l].p;
+  const uint64_t mu = c.mq[l].mu;
+  // 8 coefficients (16 words) per ChaCha block; first word64 index l*n is a multiple of 8
+  for (uint32_t b = threadIdx.x; b < c.n / 8; b += blockDim.x) {
+    uint32_t w[16];
+    chacha_block(seed, dom, obj, (uint32_t)(((uint64_t)l * c.n) / 8 + b), w);
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint64_t v = (uint64_t)w[2 * u] | ((uint64_t)w[2 * u + 1] << 32);
+      buf[padi(b * 8 + u)] = red64(v, p, mu);
+    }
+  }
+}
+
+// buf[padi(k)] = Gaussian coefficient k mod q_l
+__device__ __forceinline__ void fill_gauss(const DevCtx& c, uint64_t seed, uint32_t dom,
+                                           uint64_t obj, uint32_t p, uint32_t* buf) {
+  for (uint32_t b = threadIdx.x; b < c.n / 8; b += blockDim.x) {
+    uint32_t w[16];
+    chacha_block(seed, dom, obj, b, w);
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const uint64_t v = (uint64_t)w[2 * u] | ((uint64_t)w[2 * u + 1] << 32);
+      const int32_t e = cdt_sample(c, v);
+      buf[padi(b * 8 + u)] = e < 0 ? (uint32_t)((int32_t)p + e) : (uint32_t)e;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ query slots
+// Slot vector of query plaintext (g, i) in device NTT order, values mod t, into the
+// zeroed padded buffer mb (Sec. 3, SIMD form): query beta = g*cap + qidx (qidx =
+// rho*cap_row + qq) and dimension d = i*r + ch land in slot (rho, ch*W +
+// jin*cap_row + qq) for every jin < k_in.  Threads walk the cap x r block of H row
+// by row (consecutive threads read consecutive bytes of a query row) and scatter
+// each value to its k_in device positions through the context's scatter table.
+// No barrier.
+__device__ __forceinline__ void pack_query_slots(const DevCtx& c, const int8_t* __restrict__ H,
+                                                 int B, uint32_t g, uint32_t i, uint32_t* mb) {
+  const uint32_t qlim = min((uint32_t)c.cap, (uint32_t)(B - (int)(g * c.cap)));
+  const uint32_t d0 = i * c.r;
+  const uint32_t r = c.r, logr = c.logr, kin = c.k_in, D = c.D;
+  const uint32_t dlim = D - d0 < r ? D - d0 : r;
+  const int8_t* Hg = H + (size_t)g * c.cap * D + d0;
+  const uint32_t total = qlim << logr;
+  for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const uint32_t qidx = idx >> logr, ch = idx & (r - 1);
+    if (ch >= dlim) continue;
+    const int h = Hg[(size_t)qidx * D + ch];
+    const uint32_t v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
+    const uint32_t* sc = c.scatter + (size_t)idx * kin;
+    for (uint32_t jin = 0; jin < kin; jin++) mb[padi(__ldg(&sc[jin]))] = v;
+  }
+}
+
 // ------------------------------------------------------------------ host context
 struct ephdc_ctx_impl;  // defined in host.cu
 
@@ -464,6 +531,9 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
                                 cudaStream_t st);
 cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                        uint32_t* partial, int splits, uint32_t* acc, cudaStream_t st);
+// acc[x] = sum over splits of partial[split][x] mod q_l, x < words
+cudaError_t launch_mac_reduce(const DevCtx& c, const uint32_t* partial, int splits, size_t words,
+                              uint32_t* acc, cudaStream_t st);
 // tiling of the multi-group MAC: gt groups x ot outputs per warp, gc groups per
 // CTA, ic plaintext indices per shared-memory chunk
 struct MacTiling {
@@ -482,6 +552,14 @@ cudaError_t launch_keygen(const DevCtx& c, uint64_t seed, uint32_t* sk, uint32_t
                           cudaStream_t st);
 cudaError_t launch_encrypt_model(const DevCtx& c, const int8_t* classes, const uint32_t* sk,
                                  uint64_t seed, uint32_t* model, cudaStream_t st);
+// server-side variant (HE-HDC-SR): the client encrypts its query plaintexts, the
+// server holds the class hypervectors as plaintexts
+cudaError_t launch_encrypt_queries(const DevCtx& c, const int8_t* H, int B, const uint32_t* sk,
+                                   uint64_t seed, uint32_t* ctq, cudaStream_t st);
+cudaError_t launch_encode_model_plain(const DevCtx& c, const int8_t* classes, uint32_t* mm,
+                                      cudaStream_t st);
+cudaError_t launch_ctpt_mac(const DevCtx& c, const uint32_t* ctq, int G, const uint32_t* mm,
+                            uint32_t* partial, int splits_max, uint32_t* acc, cudaStream_t st);
 cudaError_t launch_decrypt_scores(const DevCtx& c, const uint32_t* sk, const uint32_t* ct,
                                   int B, uint32_t* xbuf, uint32_t* scores, cudaStream_t st);
 cudaError_t launch_ntt_natural(const DevCtx& c, uint32_t limb, uint32_t* poly, int count,

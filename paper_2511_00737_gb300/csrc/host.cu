@@ -472,6 +472,13 @@ size_t ephdc_plain_bytes(const ephdc_ctx* c, int32_t B) {
   if (!c || B < 1) return 0;
   return (size_t)groups_for(c, B) * c->dc.P * c->dc.L * c->dc.n * sizeof(uint32_t);
 }
+size_t ephdc_query_ct_bytes(const ephdc_ctx* c, int32_t B) {
+  if (!c || B < 1) return 0;
+  return (size_t)groups_for(c, B) * c->dc.P * 2 * c->dc.L * c->dc.n * sizeof(uint32_t);
+}
+size_t ephdc_model_plain_bytes(const ephdc_ctx* c) {
+  return c ? (size_t)c->dc.Kp * c->dc.P * c->dc.L * c->dc.n * sizeof(uint32_t) : 0;
+}
 size_t ephdc_out_ct_bytes(const ephdc_ctx* c, int32_t B) {
   if (!c || B < 1) return 0;
   return (size_t)groups_for(c, B) * c->dc.Kp * 2 * c->dc.L * c->dc.n * sizeof(uint32_t);
@@ -504,6 +511,9 @@ static ephdc_status launched(ephdc_ctx* c, cudaError_t e, const char* what) {
   return cuda_status(c, e, what);
 }
 
+static ephdc_status rotate_export(ephdc_ctx* c, int G, const void* gk, uint32_t* out,
+                                  cudaStream_t st);
+
 static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
                                     const void* model, const void* gk, uint32_t* out,
                                     cudaStream_t st) {
@@ -528,6 +538,15 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
     }
   }
   if (e != cudaSuccess) return launched(c, e, "ptct_mac");
+  return rotate_export(c, G, gk, out, st);
+}
+
+// S7 + S8 on the accumulators in c->acc: rotate-and-sum over the r chunks, then the
+// inverse NTT of every limb into the coefficient-domain output ciphertexts
+static ephdc_status rotate_export(ephdc_ctx* c, int G, const void* gk, uint32_t* out,
+                                  cudaStream_t st) {
+  const DevCtx& d = c->dc;
+  cudaError_t e;
   const int count = G * (int)d.Kp;
   uint32_t* cur = c->acc;
   if (d.logr) {
@@ -616,6 +635,51 @@ ephdc_status bfv_ptct_similarity(ephdc_ctx* c, const uint32_t* pt, int32_t B, co
   if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
   CHECK_B(c, B);
   return similarity_impl(c, pt, B, model, gk, out, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ server-side variant
+ephdc_status bfv_encrypt_queries(ephdc_ctx* c, const int8_t* H, int32_t B, const void* sk,
+                                 uint64_t seed, uint32_t* ctq, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, H, "H_dev");
+  CHECK_PTR(c, sk, "sk_dev");
+  CHECK_PTR(c, ctq, "query_ct_dev");
+  CHECK_B(c, B);
+  cudaError_t e;
+  {
+    StageTimer tm(c, EPHDC_STAGE_ENCRYPT, (cudaStream_t)stream, 1);
+    e = ephdc::launch_encrypt_queries(c->dc, H, B, (const uint32_t*)sk, seed, ctq,
+                                      (cudaStream_t)stream);
+  }
+  return launched(c, e, "encrypt_queries");
+}
+
+ephdc_status bfv_encode_model_plain(ephdc_ctx* c, const int8_t* classes, uint32_t* mm,
+                                    void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, classes, "class_hv_dev");
+  CHECK_PTR(c, mm, "model_plain_dev");
+  return launched(c, ephdc::launch_encode_model_plain(c->dc, classes, mm, (cudaStream_t)stream),
+                  "encode_model_plain");
+}
+
+ephdc_status bfv_ctpt_similarity(ephdc_ctx* c, const uint32_t* ctq, int32_t B, const uint32_t* mm,
+                                 const void* gk, uint32_t* out, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, ctq, "query_ct_dev");
+  CHECK_PTR(c, mm, "model_plain_dev");
+  CHECK_PTR(c, out, "out_ct_dev");
+  if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
+  CHECK_B(c, B);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int G = (int)groups_for(c, B);
+  cudaError_t e;
+  {
+    StageTimer tm(c, EPHDC_STAGE_MAC, st, (c->dc.Kp + 3) / 4 + 1);
+    e = ephdc::launch_ctpt_mac(c->dc, ctq, G, mm, c->partial, c->splits, c->acc, st);
+  }
+  if (e != cudaSuccess) return launched(c, e, "ctpt_mac");
+  return rotate_export(c, G, gk, out, st);
 }
 
 ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_t B,

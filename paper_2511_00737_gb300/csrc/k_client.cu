@@ -23,13 +23,10 @@ __device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t 
 }
 
 // ------------------------------------------------------------------ EncPt
-// One CTA per plaintext (g, i).  Query beta = g*cap + qidx (qidx = rho*cap_row + qq)
-// and dimension d = i*r + ch land in slot (rho, ch*W + jin*cap_row + qq) for every
-// jin < k_in.  Threads walk the cap x r block of H row by row (consecutive threads
-// read consecutive bytes of a query row) and scatter each value to its k_in device
-// positions through the context's scatter table; then the inverse NTT mod t gives the
-// plaintext coefficients, and for each limb the centred lift feeds the forward NTT,
-// whose output is staged in shared memory and stored with 16-byte writes.
+// One CTA per plaintext (g, i).  The query slots are packed (pack_query_slots), the
+// inverse NTT mod t gives the plaintext coefficients, and for each limb the centred
+// lift feeds the forward NTT, whose output is staged in shared memory and stored
+// with 16-byte writes.
 template <int LOGN, int V>
 __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
     k_encode_plain(DevCtx c, const int8_t* __restrict__ H, int B, uint32_t* __restrict__ pt) {
@@ -41,20 +38,7 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
   const uint32_t g = gi / c.P, i = gi - g * c.P;
   for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) mb[padi(j)] = 0;
   __syncthreads();
-  const uint32_t qlim = min((uint32_t)c.cap, (uint32_t)(B - (int)(g * c.cap)));
-  const uint32_t d0 = i * c.r;
-  const uint32_t r = c.r, logr = c.logr, kin = c.k_in, D = c.D;
-  const uint32_t dlim = D - d0 < r ? D - d0 : r;
-  const int8_t* Hg = H + (size_t)g * c.cap * D + d0;
-  const uint32_t total = qlim << logr;
-  for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const uint32_t qidx = idx >> logr, ch = idx & (r - 1);
-    if (ch >= dlim) continue;
-    const int h = Hg[(size_t)qidx * D + ch];
-    const uint32_t v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
-    const uint32_t* sc = c.scatter + (size_t)idx * kin;
-    for (uint32_t jin = 0; jin < kin; jin++) mb[padi(__ldg(&sc[jin]))] = v;
-  }
+  pack_query_slots(c, H, B, g, i, mb);
   __syncthreads();
   ntt_inv_t<LOGN, V>(mb, c.mt);  // slots -> coefficients in [0, t)
   constexpr uint32_t thalf = (EPHDC_T - 1) / 2;
@@ -439,7 +423,11 @@ cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t words = (size_t)G * O * c.L * c.n;
+  return launch_mac_reduce(c, partial, splits, (size_t)G * O * c.L * c.n, acc, st);
+}
+
+cudaError_t launch_mac_reduce(const DevCtx& c, const uint32_t* partial, int splits, size_t words,
+                              uint32_t* acc, cudaStream_t st) {
   k_mac_reduce<<<(unsigned)((words + 255) / 256), 256, 0, st>>>(c, partial, splits, words, acc);
   return cudaGetLastError();
 }

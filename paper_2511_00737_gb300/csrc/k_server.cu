@@ -26,45 +26,6 @@ __device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t 
   return brev((((e * g) & n2mask) - 1) >> 1, logn);
 }
 
-__device__ __forceinline__ int32_t cdt_sample(const DevCtx& c, uint64_t u) {
-  int32_t cnt = 0;
-#pragma unroll
-  for (int m = 0; m < EPHDC_CDT_LEN; m++) cnt += u >= c.cdt[m];
-  return cnt - 19;
-}
-
-// buf[padi(k)] = uniform coefficient k of limb l: 64-bit word l*n + k mod q_l
-__device__ void fill_uniform(const DevCtx& c, uint64_t seed, uint32_t dom, uint64_t obj,
-                             uint32_t l, uint32_t* buf) {
-  const uint32_t p = c.mq[l].p;
-  const uint64_t mu = c.mq[l].mu;
-  // 8 coefficients (16 words) per ChaCha block; first word64 index l*n is a multiple of 8
-  for (uint32_t b = threadIdx.x; b < c.n / 8; b += blockDim.x) {
-    uint32_t w[16];
-    chacha_block(seed, dom, obj, (uint32_t)(((uint64_t)l * c.n) / 8 + b), w);
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint64_t v = (uint64_t)w[2 * u] | ((uint64_t)w[2 * u + 1] << 32);
-      buf[padi(b * 8 + u)] = red64(v, p, mu);
-    }
-  }
-}
-
-// buf[padi(k)] = Gaussian coefficient k mod q_l
-__device__ void fill_gauss(const DevCtx& c, uint64_t seed, uint32_t dom, uint64_t obj, uint32_t p,
-                           uint32_t* buf) {
-  for (uint32_t b = threadIdx.x; b < c.n / 8; b += blockDim.x) {
-    uint32_t w[16];
-    chacha_block(seed, dom, obj, b, w);
-#pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const uint64_t v = (uint64_t)w[2 * u] | ((uint64_t)w[2 * u + 1] << 32);
-      const int32_t e = cdt_sample(c, v);
-      buf[padi(b * 8 + u)] = e < 0 ? (uint32_t)((int32_t)p + e) : (uint32_t)e;
-    }
-  }
-}
-
 // ------------------------------------------------------------------ keygen
 // sk[l] = NTT_l(s mod q_l)
 __global__ void __launch_bounds__(512) k_secret(DevCtx c, uint64_t seed, uint32_t* __restrict__ sk) {

@@ -70,9 +70,15 @@ _SIGS = {
     "ephdc_tune_get": (ctypes.c_int64, [_VP, ctypes.c_char_p]),
     "ephdc_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "ephdc_profile_read": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "ephdc_query_ct_bytes": (ctypes.c_size_t, [_VP, ctypes.c_int32]),
+    "ephdc_model_plain_bytes": (ctypes.c_size_t, [_VP]),
+    "bfv_encrypt_queries": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, ctypes.c_uint64, _VP,
+                                           _VP]),
+    "bfv_encode_model_plain": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "bfv_ctpt_similarity": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
 }
 
-STAGES = ["hdc_encode", "encode_plain", "mac", "rotate", "export"]
+STAGES = ["hdc_encode", "encode_plain", "mac", "rotate", "export", "encrypt_queries"]
 
 
 def lib_path():
@@ -196,6 +202,23 @@ def ephdc_infer_multi(ctx, Xs, Wt, model, gk, out_ct, stream=None):
                                         _ptr(out_ct, "out_ct"), _stream(stream)))
 
 
+# server-side variant (HE-HDC-SR): the client encrypts its queries
+def bfv_encrypt_queries(ctx, H, B, sk, seed, query_ct, stream=None):
+    _check(ctx, lib().bfv_encrypt_queries(ctx, _ptr(H, "H", dtype=torch.int8), B, _ptr(sk, "sk"),
+                                          seed, _ptr(query_ct, "query_ct"), _stream(stream)))
+
+
+def bfv_encode_model_plain(ctx, classes, model_plain, stream=None):
+    _check(ctx, lib().bfv_encode_model_plain(ctx, _ptr(classes, "classes", dtype=torch.int8),
+                                             _ptr(model_plain, "model_plain"), _stream(stream)))
+
+
+def bfv_ctpt_similarity(ctx, query_ct, B, model_plain, gk, out_ct, stream=None):
+    _check(ctx, lib().bfv_ctpt_similarity(ctx, _ptr(query_ct, "query_ct"), B,
+                                          _ptr(model_plain, "model_plain"), _ptr(gk, "gk"),
+                                          _ptr(out_ct, "out_ct"), _stream(stream)))
+
+
 # ------------------------------------------------------------------ convenience
 class Context:
     """One set of BFV parameters + slot layout; allocates correctly sized tensors."""
@@ -277,6 +300,23 @@ class Context:
         B = X.shape[0]
         out = self.out_ct(B) if out is None else out
         ephdc_infer(self.ctx, X, Wt, B, model, gk, out, stream)
+        return out
+
+    # server-side variant
+    def encrypt_queries(self, H, sk, seed, out=None, stream=None):
+        B = H.shape[0]
+        ctq = self._u32(lib().ephdc_query_ct_bytes(self.ctx, B)) if out is None else out
+        bfv_encrypt_queries(self.ctx, H, B, sk, seed, ctq, stream)
+        return ctq
+
+    def encode_model_plain(self, classes, stream=None):
+        mm = self._u32(lib().ephdc_model_plain_bytes(self.ctx))
+        bfv_encode_model_plain(self.ctx, classes, mm, stream)
+        return mm
+
+    def ctpt_similarity(self, query_ct, B, model_plain, gk, out=None, stream=None):
+        out = self.out_ct(B) if out is None else out
+        bfv_ctpt_similarity(self.ctx, query_ct, B, model_plain, gk, out, stream)
         return out
 
     def decrypt_scores(self, sk, out_ct, B, stream=None):
