@@ -53,6 +53,9 @@ def lib():
             "or_slot_encode_definition": (None, [u32, u32, u32, vp, vp]),
             "or_ctx_size": (ctypes.c_size_t, []),
             "or_ctx_init": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, u32, dbl]),
+            "or_ctx_init2": (ctypes.c_int, [vp, u32, u32, u32, u32, u32, u32, dbl, u32, u32,
+                                            u32, u32]),
+            "or_find_primes_bits": (ctypes.c_int, [u32, u32, u32, vp]),
             "or_ctx_get": (u32, [vp, ctypes.c_int]),
             "or_ctx_cdt": (None, [vp, vp]),
             "or_fold_galois": (u32, [vp, u32]),
@@ -100,9 +103,9 @@ def is_prime(v):
     return bool(lib().or_is_prime(int(v)))
 
 
-def find_primes(n, L):
+def find_primes(n, L, bits=30):
     out = np.zeros(L, np.uint32)
-    if lib().or_find_primes(n, L, _p(out)):
+    if lib().or_find_primes_bits(n, L, bits, _p(out)):
         raise ValueError("not enough primes")
     return out
 
@@ -237,11 +240,16 @@ def hdc_encode(X, Wt, shift, bits):
 class Oracle:
     """BFV parameters + (k_in, r) slot layout, and the client path step by step."""
 
-    def __init__(self, n, L, k, k_in, r, D, sigma=3.2):
+    def __init__(self, n, L, k, k_in, r, D, sigma=3.2, t=T, prime_bits=30, scale_shift=0,
+                 scale_group=512):
         self._buf = ctypes.create_string_buffer(lib().or_ctx_size())
         self.ctx = ctypes.cast(self._buf, ctypes.c_void_p)
-        if lib().or_ctx_init(self.ctx, n, L, k, k_in, r, D, sigma):
+        if lib().or_ctx_init2(self.ctx, n, L, k, k_in, r, D, sigma, t, prime_bits, scale_shift,
+                              scale_group):
             raise ValueError("invalid oracle parameters")
+        self.scale_shift, self.scale_group = scale_shift, scale_group
+        self.prime_bits = prime_bits
+        self.scale_u = int(lib().or_ctx_get(self.ctx, 14))
         g = lambda w: int(lib().or_ctx_get(self.ctx, w))
         self.n, self.L, self.t, self.k, self.k_in, self.r, self.D = (g(i) for i in range(7))
         self.W, self.cap_row, self.cap, self.P, self.Kp, self.logr, self.zeta = (
@@ -335,6 +343,32 @@ class Oracle:
         acc = np.zeros((self.groups(B), self.Kp, 2, self.L, self.n), np.uint32)
         lib().or_ctpt_mac(self.ctx, _p(_u32(ctq)), B, _p(_u32(mm)), _p(acc))
         return acc
+
+    # noise growth (Sec. 5.2, Alg. 1 findDmax) ---------------------------------
+    def find_dmax_trial(self, m, model, s, H, cls):
+        """One trial of findDmax (one class, r = 1, one group): D_i grows while the
+        evaluation with D_i + 1 dimensions decrypts to the clear dot products mod t
+        for every query (at most the context's D).  The evaluation with D'
+        dimensions is the accumulator sum_{i < D'} lift(m_i) * ct_i; modular
+        addition does not depend on the order, so it is built one product at a
+        time and decrypted after each."""
+        assert self.k == 1 and self.k_in == 1 and self.r == 1
+        B = H.shape[0]
+        acc = np.zeros((1, 1, 2, self.L, self.n), np.uint32)
+        clear = np.zeros(B, np.int64)
+        t = self.t
+        for i in range(self.D):
+            mi = m[0, i].astype(np.int64)
+            lm = np.where(mi <= (t - 1) // 2, mi, mi - t)
+            for l, p in enumerate(self.q):
+                for poly in range(2):
+                    prod = polymul(lm % p, model[i, 0, poly, l], p, self.psi[l])
+                    acc[0, 0, poly, l] = (acc[0, 0, poly, l].astype(np.int64) + prod) % p
+            clear = (clear + H[:, i].astype(np.int64) * int(cls[0, i])) % t
+            got = self.decrypt_scores(s, acc, B)[:, 0]
+            if not np.array_equal(got, clear.astype(np.uint32)):
+                return i
+        return self.D
 
     # server check ------------------------------------------------------------
     def decrypt(self, s, ct):

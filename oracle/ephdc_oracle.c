@@ -88,16 +88,18 @@ int or_is_prime(u32 n) {
 
 /* RNS primes: the L largest primes q < 2^30 with q = 1 (mod 2n), in decreasing
  * order.  Sec. 2.2 needs q = 1 (mod 2n) so that x^n + 1 splits (NTT-friendly). */
-int or_find_primes(u32 n, u32 L, u32* q_out) {
+int or_find_primes_bits(u32 n, u32 L, u32 bits, u32* q_out) {
   u64 two_n = 2ull * n;
   u32 found = 0;
   for (u64 j = 1; found < L; j++) {
-    if (j * two_n >= (1ull << 30)) return -1;
-    u32 c = (u32)((1ull << 30) - j * two_n + 1);
+    if (j * two_n >= (1ull << bits)) return -1;
+    u32 c = (u32)((1ull << bits) - j * two_n + 1);
     if (or_is_prime(c)) q_out[found++] = c;
   }
   return 0;
 }
+
+int or_find_primes(u32 n, u32 L, u32* q_out) { return or_find_primes_bits(n, L, 30, q_out); }
 
 /* Least x >= 2 with x^((p-1)/2) = -1 (a quadratic non-residue, Euler's criterion);
  * psi = x^((p-1)/(2n)) then has order exactly 2n. */
@@ -438,8 +440,12 @@ typedef struct {
   u32 q[OR_MAXL], psi[OR_MAXL];
   u32 zeta;
   u32 delta[OR_MAXL]; /* floor(q/t) mod q_l */
+  u32 rt;             /* q mod t */
   u64 cdt[OR_CDT_LEN];
   double sigma;
+  /* scaling operation (Sec. 5.1): after every scale_group products added to an
+   * accumulator, multiply it by scale_u = (2^scale_shift)^-1 mod t; 0 = off */
+  u32 scale_shift, scale_group, scale_u;
 } or_ctx;
 
 size_t or_ctx_size(void) { return sizeof(or_ctx); }
@@ -448,12 +454,23 @@ size_t or_ctx_size(void) { return sizeof(or_ctx); }
  * row, k_in classes side by side inside a chunk, cap_row = floor(W / k_in)
  * queries per row.  r = 1, k_in = k is the paper's SIMD representation
  * (Sec. 3; batch floor(N/k), D plaintexts, no rotation). */
-int or_ctx_init(or_ctx* c, u32 n, u32 L, u32 k, u32 k_in, u32 r, u32 D, double sigma) {
+/* t: the plaintext modulus, a prime = 1 (mod 2n) below 2^30 (slot packing needs a
+ * primitive 2n-th root of unity mod t); prime_bits: the RNS primes are the L largest
+ * primes below 2^prime_bits that are = 1 (mod 2n). */
+int or_ctx_init2(or_ctx* c, u32 n, u32 L, u32 k, u32 k_in, u32 r, u32 D, double sigma, u32 t,
+                 u32 prime_bits, u32 scale_shift, u32 scale_group) {
   memset(c, 0, sizeof *c);
   if (n < 8 || (n & (n - 1)) || n > 32768) return -1;
   if (L < 1 || L > OR_MAXL || k < 1 || k_in < 1 || k % k_in || D < 1) return -1;
   if (r < 1 || (r & (r - 1)) || r > n / 2) return -1;
-  c->n = n; c->L = L; c->t = OR_T; c->k = k; c->k_in = k_in; c->r = r; c->D = D;
+  if (t < 3 || t >= (1u << 30) || t % (2 * n) != 1 || !or_is_prime(t)) return -1;
+  if (prime_bits < 14 || prime_bits > 30) return -1;
+  if (scale_shift > 30 || (scale_shift && scale_group < 1)) return -1;
+  c->n = n; c->L = L; c->t = t; c->k = k; c->k_in = k_in; c->r = r; c->D = D;
+  c->scale_shift = scale_shift;
+  c->scale_group = scale_group;
+  /* (2^s)^-1 mod t by Fermat: t is prime */
+  c->scale_u = scale_shift ? (u32)powmod((u32)((1ull << scale_shift) % t), t - 2, t) : 1;
   c->sigma = sigma;
   c->W = n / (2 * r);
   c->cap_row = c->W / k_in;
@@ -462,17 +479,30 @@ int or_ctx_init(or_ctx* c, u32 n, u32 L, u32 k, u32 k_in, u32 r, u32 D, double s
   c->P = (D + r - 1) / r;
   c->Kp = k / k_in;
   c->logr = (u32)log2u(r);
-  if (or_find_primes(n, L, c->q)) return -1;
+  if (or_find_primes_bits(n, L, prime_bits, c->q)) return -1;
   for (u32 l = 0; l < L; l++) c->psi[l] = or_root_2n(c->q[l], n);
-  c->zeta = or_root_2n(OR_T, n);
+  c->zeta = or_root_2n(t, n);
   /* Delta = floor(q / t), reduced mod each q_l */
   big_t Q;
   big_from_u32(&Q, 1);
   for (u32 l = 0; l < L; l++) big_mul_small(&Q, c->q[l]);
-  big_divmod_small(&Q, OR_T);
+  c->rt = big_divmod_small(&Q, t);
   for (u32 l = 0; l < L; l++) c->delta[l] = big_mod_small(&Q, c->q[l]);
   or_cdt_table(sigma, c->cdt);
   return 0;
+}
+
+/* The scaled message of encryption, round(q m / t) with ties up, m in [0, t), reduced
+ * mod q_l: q m = (floor(q/t) t + (q mod t)) m, so it is
+ * floor(q/t) m + floor(((q mod t) m + floor((t+1)/2)) / t). */
+static u32 scaled_msg(const or_ctx* c, u32 l, u32 m) {
+  u32 p = c->q[l];
+  u64 fix = ((u64)c->rt * m + (c->t + 1) / 2) / c->t;
+  return addmod(mulmod(c->delta[l], m, p), (u32)(fix % p), p);
+}
+
+int or_ctx_init(or_ctx* c, u32 n, u32 L, u32 k, u32 k_in, u32 r, u32 D, double sigma) {
+  return or_ctx_init2(c, n, L, k, k_in, r, D, sigma, OR_T, 30, 0, 512);
 }
 
 u32 or_ctx_get(const or_ctx* c, int what) {
@@ -482,6 +512,8 @@ u32 or_ctx_get(const or_ctx* c, int what) {
     case 6: return c->D;   case 7: return c->W;   case 8: return c->cap_row;
     case 9: return c->cap; case 10: return c->P;  case 11: return c->Kp;
     case 12: return c->logr; case 13: return c->zeta;
+    case 14: return c->scale_u;
+    case 15: return c->rt;
     default: break;
   }
   if (what >= 100 && what < 100 + OR_MAXL) return c->q[what - 100];
@@ -606,7 +638,7 @@ void or_encrypt_model(const or_ctx* c, u64 seed, const int8_t* classes, const i3
         u32* c1 = model + (((u64)cidx * 2 + 1) * L + l) * n;
         for (u32 kk = 0; kk < n; kk++) {
           u32 v = submod(smod(e[kk], p), as[kk], p);
-          v = addmod(v, mulmod(c->delta[l], m[kk], p), p);
+          v = addmod(v, scaled_msg(c, l, m[kk]), p);
           c0[kk] = v;
           c1[kk] = a[(u64)l * n + kk];
         }
@@ -697,6 +729,12 @@ void or_ptct_mac(const or_ctx* c, const u32* m, i32 B, const u32* model, u32* ac
         const u32* ct = model + ((((u64)i * c->Kp + jp) * 2 + poly) * L + l) * n;
         or_polymul(n, p, c->psi[l], lm, ct, prod);
         for (u32 kk = 0; kk < n; kk++) out[kk] = addmod(out[kk], prod[kk], p);
+        if (c->scale_shift && (i + 1) % c->scale_group == 0) {
+          /* scaling operation: the accumulator times the plaintext scalar
+           * (2^s)^-1 mod t, lifted into Z_{q_l} */
+          u32 u = lift(c->scale_u, c->t, p);
+          for (u32 kk = 0; kk < n; kk++) out[kk] = mulmod(out[kk], u, p);
+        }
       }
     }
     free(lm); free(prod);
@@ -802,12 +840,12 @@ void or_decrypt(const or_ctx* c, const i32* s, const u32* ct, u32* mout) {
       big_add(&X, &term);
     }
     while (big_cmp(&X, &Q) >= 0) big_sub(&X, &Q);
-    /* num = t x + floor(q/2); quotient bit by bit (it is < 2^18) */
+    /* num = t x + floor(q/2); quotient bit by bit (it is at most t < 2^30) */
     big_t num = X;
     big_mul_small(&num, c->t);
     big_add(&num, &Qh);
     u32 quo = 0;
-    for (int b = 17; b >= 0; b--) {
+    for (int b = 30; b >= 0; b--) {
       big_t qs = Q;
       big_shl(&qs, b);
       if (big_cmp(&num, &qs) >= 0) { big_sub(&num, &qs); quo |= 1u << b; }
@@ -873,7 +911,7 @@ void or_encrypt_slots(const or_ctx* c, u64 seed, u64 obj, const i32* s, const u3
     or_polymul(n, p, c->psi[l], a + (u64)l * n, sl, as);
     for (u32 kk = 0; kk < n; kk++) {
       u32 v = submod(smod(e[kk], p), as[kk], p);
-      ct[(u64)l * n + kk] = addmod(v, mulmod(c->delta[l], m[kk], p), p);
+      ct[(u64)l * n + kk] = addmod(v, scaled_msg(c, l, m[kk]), p);
       ct[((u64)L + l) * n + kk] = a[(u64)l * n + kk];
     }
   }
@@ -972,7 +1010,7 @@ void or_encrypt_queries(const or_ctx* c, u64 seed, const int8_t* H, i32 B, const
         u32* c1 = ctq + (((u64)gi * 2 + 1) * L + l) * n;
         for (u32 kk = 0; kk < n; kk++) {
           u32 v = submod(smod(e[kk], p), as[kk], p);
-          c0[kk] = addmod(v, mulmod(c->delta[l], m[kk], p), p);
+          c0[kk] = addmod(v, scaled_msg(c, l, m[kk]), p);
           c1[kk] = a[(u64)l * n + kk];
         }
       }
@@ -1022,6 +1060,10 @@ void or_ctpt_mac(const or_ctx* c, const u32* ctq, i32 B, const u32* mm, u32* acc
         const u32* ct = ctq + ((((u64)g * c->P + i) * 2 + poly) * L + l) * n;
         or_polymul(n, p, c->psi[l], ct, lm, prod);
         for (u32 kk = 0; kk < n; kk++) out[kk] = addmod(out[kk], prod[kk], p);
+        if (c->scale_shift && (i + 1) % c->scale_group == 0) {
+          u32 u = lift(c->scale_u, c->t, p);  /* scaling operation, as on the client side */
+          for (u32 kk = 0; kk < n; kk++) out[kk] = mulmod(out[kk], u, p);
+        }
       }
     }
     free(lm); free(prod);

@@ -213,7 +213,9 @@ class TinyBFV:
         c0, c1 = [], []
         for l, p in enumerate(self.q):
             as_ = negamul(a[l], [v % p for v in s], p)
-            c0.append([(e[kk] - as_[kk] + (self.delta % p) * m[kk]) % p for kk in range(self.n)])
+            # scaled message round(Q m / t), ties up, written with Python integers
+            c0.append([(e[kk] - as_[kk] + (self.Q * m[kk] + (T + 1) // 2) // T) % p
+                       for kk in range(self.n)])
             c1.append(list(a[l]))
         return (c0, c1)
 

@@ -3,6 +3,8 @@ of Sec. 6, Table t:clientrt): the client encrypts its query hypervectors in the 
 form, the server holds the class hypervectors as plaintexts.  Checked against the
 slot layout written out by brute force, the clear dot products, the ChaCha20 streams
 of the samplers, and the message-size ratio the paper reports."""
+import math
+
 import numpy as np
 import pytest
 
@@ -65,7 +67,7 @@ def test_query_ciphertexts_decrypt_to_query_slots(n, L, k, k_in, r, D, B):
 
 
 def test_query_ciphertext_is_secret_key_rlwe_with_its_own_streams():
-    """c1 is the uniform stream of domain 6 and c0 + c1 s = floor(q/t) m + e with e the
+    """c1 is the uniform stream of domain 6 and c0 + c1 s = round(q m / t) + e with e the
     Gaussian stream of domain 7, for ciphertext number g*P + i."""
     o = O.Oracle(32, 2, 2, 1, 2, 10)
     H = np.random.default_rng(2).integers(-8, 8, (40, 10)).astype(np.int8)
@@ -75,12 +77,15 @@ def test_query_ciphertext_is_secret_key_rlwe_with_its_own_streams():
         gi = g * o.P + i
         a = O.sample_uniform(5, 6, gi, o.n, o.q)
         e = O.sample_gauss(5, 7, gi, o.n).astype(np.int64)
-        m = O.slot_encode(_slots_of_queries(o, H, g, i), o.zeta).astype(np.int64)
+        m = O.slot_encode(_slots_of_queries(o, H, g, i), o.zeta)
+        Q = math.prod(o.q)
+        scaled = [(Q * int(v) + (o.t + 1) // 2) // o.t for v in m]  # round(Q m / t)
         for l, p in enumerate(o.q):
             assert np.array_equal(ctq[g, i, 1, l], a[l])
             sl = np.asarray(s, np.int64) % p
             phase = (ctq[g, i, 0, l].astype(np.int64) + O.polymul(a[l], sl, p, o.psi[l])) % p
-            assert np.array_equal(phase, (o.delta[l] * m + e) % p)
+            want = (np.array([v % p for v in scaled], np.int64) + e) % p
+            assert np.array_equal(phase, want)
 
 
 @pytest.mark.parametrize("n,L,k,k_in,r,D,B", CASES)
