@@ -67,6 +67,14 @@ typedef struct {
   int32_t shift;      /* quantiser shift s >= 0                                   */
   uint32_t max_batch; /* largest batch B any call on this context will use        */
   double sigma;       /* error standard deviation (3.2)                           */
+  uint32_t t;         /* plaintext modulus: a prime = 1 (mod 2n) below 2^30;
+                         0 selects 65537                                           */
+  uint32_t prime_bits;/* the L RNS primes are the largest primes below 2^prime_bits
+                         with q = 1 (mod 2n); 20..30, 0 selects 30                 */
+  uint32_t scale_shift; /* scaling operation of Sec. 5.1: 0 = off; else the running
+                         accumulator is multiplied by (2^scale_shift)^-1 mod t
+                         after every scale_group additions                         */
+  uint32_t scale_group; /* g of the scaling operation (0 selects 512)              */
 } ephdc_params;
 
 typedef struct ephdc_ctx ephdc_ctx; /* opaque, owned by the library */
@@ -83,7 +91,8 @@ const char* ephdc_last_error(const ephdc_ctx* ctx);
 
 /* Derived quantities: which = "cap" (queries per group), "P" (plaintexts per
  * group), "Kp" (ciphertexts per plaintext index = k/k_in), "W", "cap_row",
- * "logr", "q0".."q7" (the primes).  Returns 0 for an unknown name. */
+ * "logr", "t" (the plaintext modulus), "q0".."q7" (the primes).  Returns 0 for an
+ * unknown name. */
 uint64_t ephdc_query(const ephdc_ctx* ctx, const char* which);
 
 /* Buffer sizes in bytes. */
@@ -104,7 +113,8 @@ ephdc_status bfv_keygen(ephdc_ctx* ctx, uint64_t seed, void* sk_dev, void* gk_de
 
 /* Encrypt the k class hypervectors (Sec. 4.1: the model, not the queries, is
  * encrypted).  class_hv_dev: int8 [k][D] row-major.  Secret-key BFV encryption:
- * c1 = a, c0 = -a*s + e + floor(q/t)*m per ciphertext, slots laid out per (k_in, r).
+ * c1 = a, c0 = -a*s + e + round(q*m/t) per ciphertext (m in [0, t), ties rounded up),
+ * slots laid out per (k_in, r).
  * model_dev: ephdc_model_bytes, device-private NTT-domain order. */
 ephdc_status bfv_encrypt_model(ephdc_ctx* ctx, const int8_t* class_hv_dev, const void* sk_dev,
                                uint64_t seed, void* model_dev, void* stream);
@@ -190,6 +200,22 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* ctx, const ephdc_request* reqs, int32_
                                const int8_t* Wt_dev, const void* model_dev, const void* gk_dev,
                                uint32_t* out_ct_dev, void* stream);
 
+/* ---------------------------------------------------------------- seeded model message */
+/* The encrypted model is sent once, server to client (Sec. 4.1).  Every model
+ * ciphertext's c1 is the uniform polynomial a drawn from ChaCha20 (domain 2,
+ * ciphertext number i*Kp + jp, keyed by the encryption seed), so the message can be
+ * c0 alone plus the 8-byte seed: half the bytes of the full model.  The client
+ * rebuilds the identical device model once, at load time.
+ * seeded_dev: ephdc_model_seeded_bytes(), [P*Kp][L][n] u32, coefficient domain. */
+size_t ephdc_model_seeded_bytes(const ephdc_ctx* ctx);
+/* Server: the c0 halves of model_dev (from bfv_encrypt_model) as the seeded message. */
+ephdc_status bfv_model_to_seeded(ephdc_ctx* ctx, const void* model_dev, uint32_t* seeded_dev,
+                                 void* stream);
+/* Client: model_dev (ephdc_model_bytes) from the seeded message and the seed it was
+ * encrypted with; equal word for word to the model bfv_encrypt_model produced. */
+ephdc_status bfv_model_from_seeded(ephdc_ctx* ctx, const uint32_t* seeded_dev, uint64_t seed,
+                                   void* model_dev, void* stream);
+
 /* ---------------------------------------------------------------- server-side variant */
 /* HE-HDC-SR (Sec. 3, the comparison of Sec. 6, Table t:clientrt): the roles of the
  * client-side path swapped.  The CLIENT holds the secret key and encrypts its query
@@ -202,7 +228,7 @@ size_t ephdc_query_ct_bytes(const ephdc_ctx* ctx, int32_t B); /* G*P ciphertexts
 size_t ephdc_model_plain_bytes(const ephdc_ctx* ctx);         /* (k/k_in)*P plaintexts  */
 
 /* Client: secret-key encryption of query plaintext (g, i) (its slots as in
- * bfv_encode_plain): c1 = a, c0 = -a s + e + floor(q/t) m.  Randomness: ChaCha20
+ * bfv_encode_plain): c1 = a, c0 = -a s + e + round(q m / t).  Randomness: ChaCha20
  * keyed by the seed, ciphertext number g*P + i, domain 6 (a) and 7 (e).
  * H_dev: int8 [B][D], 1 <= B <= max_batch.  query_ct_dev: ephdc_query_ct_bytes(B),
  * [G][P][2][L][n] in the device NTT order (ephdc_ct_to_host_coeff reads it).
@@ -222,6 +248,22 @@ ephdc_status bfv_encode_model_plain(ephdc_ctx* ctx, const int8_t* class_hv_dev,
 ephdc_status bfv_ctpt_similarity(ephdc_ctx* ctx, const uint32_t* query_ct_dev, int32_t B,
                                  const uint32_t* model_plain_dev, const void* gk_dev,
                                  uint32_t* out_ct_dev, void* stream);
+
+/* ---------------------------------------------------------------- noise growth */
+/* One trial of the noise-growth experiment (Sec. 5.2, Alg. 1 findDmax): how many
+ * plaintext x ciphertext products the accumulator takes before decryption fails.
+ * Needs the paper's layout with one class (k = k_in = 1, r = 1) and one group of
+ * 1 <= B <= cap queries; pt_dev = bfv_encode_plain(H_dev) and model_dev =
+ * bfv_encrypt_model(class_hv_dev) for the context's D dimensions, sk_dev their key.
+ * The accumulator after D' products (D' = 1..D) is the evaluation with D'
+ * dimensions; each is decrypted and compared with sum_{d < D'} h[q][d] c[d] mod t
+ * for every query q.  *dmax = the largest D' such that every evaluation with
+ * 1..D' dimensions is correct (D if none fails).  Synchronous on the default
+ * stream; allocates and frees D (L n + n) words of device scratch.  EPHDC_EUNSUPPORTED
+ * for another layout, EPHDC_EINVAL for a bad B or pointer. */
+ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int8_t* H_dev,
+                                   int32_t B, const int8_t* class_hv_dev, const uint32_t* pt_dev,
+                                   const void* model_dev, int32_t* dmax);
 
 /* Schedule knobs of the multi-accumulate (set by the autotuner; results never
  * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled / 3 tensor cores (exact
@@ -283,6 +325,15 @@ ephdc_status ephdc_profile_enable(ephdc_ctx* ctx, int on);
  * may be NULL) and the number of kernel launches the library has enqueued since the
  * last read (*launches, may be NULL), then clears the record. */
 ephdc_status ephdc_profile_read(ephdc_ctx* ctx, double* ms, uint64_t* calls, uint64_t* launches);
+
+/* Integer-pipe peaks of the current device, measured by two register-only kernels:
+ * *bfly_per_s = lazy Harvey forward butterflies with a Shoup quotient per second
+ * (the transforms' instruction mix), *mac_per_s = 64-bit carry-chain
+ * multiply-accumulates (mad.lo.cc + madc.hi) per second.  Synchronous, about 30 ms
+ * of device time; allocates and frees a small buffer.  Not part of the method: the
+ * denominators of the integer-bound rooflines.  EPHDC_EINVAL for NULL outputs,
+ * EPHDC_ENOMEM / EPHDC_ECUDA on device errors. */
+ephdc_status ephdc_measure_int_peaks(double* bfly_per_s, double* mac_per_s);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@
 #include "../../include/ephdc.h"
 
 #define EPHDC_MAXL 8
-#define EPHDC_T 65537u
+#define EPHDC_T_DEFAULT 65537u
 #define EPHDC_CDT_LEN 38
 #define EPHDC_BIGW 10  // words of the multi-word integers used by decryption
 
@@ -51,7 +51,14 @@ struct DevCtx {
   uint32_t* status;          // nonzero when a bounded device wait gave up
   int32_t ntt_plan;          // pass schedule of the encoding transforms (NttPlan V)
   uint64_t cdt[EPHDC_CDT_LEN];
+  uint32_t t;                // plaintext modulus (prime = 1 mod 2n, < 2^30)
+  uint32_t rt;               // Q mod t
+  // scaling operation: plaintext i is multiplied by scale_w[l]^(P/g - i/g) mod q_l,
+  // scale_w[l] = the centred lift of (2^s)^-1 mod t; scale_g = g (0 = off)
+  uint32_t scale_g;
+  uint32_t scale_w[EPHDC_MAXL];
 };
+
 
 // ------------------------------------------------------------------ arithmetic
 __device__ __forceinline__ uint32_t mulshoup(uint32_t x, uint32_t w, uint32_t wsh, uint32_t p) {
@@ -74,6 +81,30 @@ __device__ __forceinline__ uint32_t red64(uint64_t x, uint32_t p, uint64_t mu) {
 }
 __device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, const ModP& m) {
   return red64((uint64_t)a * b, m.p, m.mu);
+}
+
+// scale_w[l]^e mod q_l (square and multiply; e is at most P)
+__device__ __forceinline__ uint32_t scale_factor(const DevCtx& c, uint32_t l, uint32_t e) {
+  const ModP& m = c.mq[l];
+  uint32_t r = 1, b = c.scale_w[l];
+  while (e) {
+    if (e & 1) r = mulm(r, b, m);
+    b = mulm(b, b, m);
+    e >>= 1;
+  }
+  return r;
+}
+
+// The scaled message of encryption, round(Q m / t) (ties up) for m in [0, t), reduced
+// mod q_l.  Q m = (floor(Q/t) t + (Q mod t)) m, so it is floor(Q/t) m + fix with
+// fix = floor(((Q mod t) m + floor((t+1)/2)) / t) < t; the quotient comes from the
+// Barrett constant of t and one correction step.
+__device__ __forceinline__ uint32_t scaled_msg(const DevCtx& c, uint32_t l, uint32_t m) {
+  const uint64_t num = (uint64_t)c.rt * m + (c.t + 1) / 2;
+  uint64_t fix = __umul64hi(num, c.mt.mu);
+  if (num - fix * c.t >= c.t) fix++;
+  const ModP& mq = c.mq[l];
+  return addm(mulm(c.delta[l], m, mq), red64(fix, mq.p, mq.mu), mq.p);
 }
 
 // shared-memory index with one pad word per 32 (bank-conflict-free NTT passes)
@@ -506,7 +537,7 @@ __device__ __forceinline__ void pack_query_slots(const DevCtx& c, const int8_t* 
     const uint32_t qidx = idx >> logr, ch = idx & (r - 1);
     if (ch >= dlim) continue;
     const int h = Hg[(size_t)qidx * D + ch];
-    const uint32_t v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
+    const uint32_t v = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
     const uint32_t* sc = c.scatter + (size_t)idx * kin;
     for (uint32_t jin = 0; jin < kin; jin++) mb[padi(__ldg(&sc[jin]))] = v;
   }
@@ -560,6 +591,21 @@ cudaError_t launch_encode_model_plain(const DevCtx& c, const int8_t* classes, ui
                                       cudaStream_t st);
 cudaError_t launch_ctpt_mac(const DevCtx& c, const uint32_t* ctq, int G, const uint32_t* mm,
                             uint32_t* partial, int splits_max, uint32_t* acc, cudaStream_t st);
+// the noise-growth experiment (findDmax): prefix phases in the coefficient domain,
+// decryption of phases already in the coefficient domain, first wrong prefix
+int prefix_chunks(const DevCtx& c, int D);
+cudaError_t launch_prefix_phases(const DevCtx& c, const uint32_t* pt, const uint32_t* model,
+                                 const uint32_t* sk, int D, uint32_t* X, uint32_t* T,
+                                 cudaStream_t st);
+cudaError_t launch_decrypt_phases(const DevCtx& c, const uint32_t* xbuf, int count, int B,
+                                  uint32_t* scores, cudaStream_t st);
+cudaError_t launch_first_wrong(const DevCtx& c, const int8_t* H, const int8_t* cls, int B, int D,
+                               const uint32_t* scores, int* first, cudaStream_t st);
+// seeded model message: c0 halves in the coefficient domain, and back with c1 regenerated
+cudaError_t launch_model_to_seeded(const DevCtx& c, const uint32_t* model, uint32_t* c0w,
+                                  cudaStream_t st);
+cudaError_t launch_model_from_seeded(const DevCtx& c, const uint32_t* c0w, uint64_t seed,
+                                    uint32_t* model, cudaStream_t st);
 cudaError_t launch_decrypt_scores(const DevCtx& c, const uint32_t* sk, const uint32_t* ct,
                                   int B, uint32_t* xbuf, uint32_t* scores, cudaStream_t st);
 cudaError_t launch_ntt_natural(const DevCtx& c, uint32_t limb, uint32_t* poly, int count,

@@ -212,6 +212,16 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   if (p->shift < 0 || p->shift > 30) return fail(nullptr, EPHDC_EINVAL, "shift must be in [0, 30]");
   if (p->max_batch < 1) return fail(nullptr, EPHDC_EINVAL, "max_batch must be positive");
   if (!(p->sigma > 0.0 && p->sigma < 100.0)) return fail(nullptr, EPHDC_EINVAL, "sigma out of range");
+  const uint32_t t = p->t ? p->t : EPHDC_T_DEFAULT;
+  if (t >= (1u << 30) || t % (2 * n) != 1 || !prime32(t))
+    return fail(nullptr, EPHDC_EINVAL,
+                "t must be a prime = 1 (mod 2n) below 2^30, got %u", t);
+  const uint32_t pbits = p->prime_bits ? p->prime_bits : 30;
+  if (pbits < 20 || pbits > 30)
+    return fail(nullptr, EPHDC_EINVAL, "prime_bits must be in [20, 30], got %u", pbits);
+  const uint32_t sgroup = p->scale_group ? p->scale_group : 512;
+  if (p->scale_shift > 30)
+    return fail(nullptr, EPHDC_EINVAL, "scale_shift must be in [0, 30], got %u", p->scale_shift);
 
   ephdc_ctx* c = new ephdc_ctx();
   c->prm = *p;
@@ -229,11 +239,12 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   d.P = (p->D + p->r - 1) / p->r;
   d.D = p->D; d.F = p->F; d.bits = p->hv_bits; d.shift = p->shift;
 
-  // the L largest primes q < 2^30 with q = 1 (mod 2n)
+  d.t = t;
+  // the L largest primes q < 2^prime_bits with q = 1 (mod 2n)
   std::vector<uint32_t> q;
   for (uint64_t j = 1; q.size() < p->L; j++) {
-    uint64_t cand = (1ull << 30) - j * 2ull * n + 1;
-    if (cand < (1ull << 29)) {
+    uint64_t cand = (1ull << pbits) - j * 2ull * n + 1;
+    if (cand < (1ull << (pbits - 1))) {
       delete c;
       return fail(nullptr, EPHDC_EINVAL, "not enough NTT primes");
     }
@@ -262,7 +273,7 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   }
   uint2* dtw = (uint2*)c->tables;
   for (int mi = 0; mi < nm; mi++) {
-    const uint32_t pm = mi < (int)p->L ? q[mi] : EPHDC_T;
+    const uint32_t pm = mi < (int)p->L ? q[mi] : t;
     const uint32_t psi = root2n(pm, n), psi_inv = pw(psi, pm - 2, pm);
     uint2* f = htw + (size_t)mi * 4 * n;
     uint2* b = f + n;
@@ -336,7 +347,7 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   memcpy(d.big_Q, Qw, sizeof Qw);
   uint32_t Qt[EPHDC_BIGW];
   memcpy(Qt, Qw, sizeof Qw);
-  bdiv(Qt, EPHDC_T);
+  d.rt = bdiv(Qt, t);  // Qt = floor(Q / t), d.rt = Q mod t
   uint32_t Qh[EPHDC_BIGW];
   memcpy(Qh, Qw, sizeof Qw);
   bdiv(Qh, 2);
@@ -348,6 +359,13 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
       if (o != l) bmul(hat, q[o]);
     memcpy(d.big_Qhat[l], hat, sizeof hat);
     d.qhat_inv[l] = pw(bmod(hat, q[l]), q[l] - 2, q[l]);
+  }
+  // scaling operation: w = centred lift of (2^s)^-1 mod t into each limb
+  if (p->scale_shift) {
+    d.scale_g = sgroup;
+    const uint32_t u = pw((uint32_t)((1ull << p->scale_shift) % t), t - 2, t);
+    for (uint32_t l = 0; l < p->L; l++)
+      d.scale_w[l] = u <= (t - 1) / 2 ? u : u + q[l] - t;
   }
   // discrete Gaussian table: T[m] = floor(2^64 P(X <= -19 + m)), weights
   // exp(-x^2 / (2 sigma^2)) on [-19, 19]
@@ -450,6 +468,7 @@ uint64_t ephdc_query(const ephdc_ctx* c, const char* w) {
   if (!strcmp(w, "W")) return d.W;
   if (!strcmp(w, "cap_row")) return d.cap_row;
   if (!strcmp(w, "logr")) return d.logr;
+  if (!strcmp(w, "t")) return d.t;
   if (!strcmp(w, "splits")) return (uint64_t)c->splits;
   if (!strcmp(w, "scratch_bytes")) return c->scratch_bytes;
   if (w[0] == 'q' && w[1] >= '0' && w[1] <= '7' && w[2] == 0) {
@@ -471,6 +490,9 @@ size_t ephdc_model_bytes(const ephdc_ctx* c) {
 size_t ephdc_plain_bytes(const ephdc_ctx* c, int32_t B) {
   if (!c || B < 1) return 0;
   return (size_t)groups_for(c, B) * c->dc.P * c->dc.L * c->dc.n * sizeof(uint32_t);
+}
+size_t ephdc_model_seeded_bytes(const ephdc_ctx* c) {
+  return c ? (size_t)c->dc.P * c->dc.Kp * c->dc.L * c->dc.n * sizeof(uint32_t) : 0;
 }
 size_t ephdc_query_ct_bytes(const ephdc_ctx* c, int32_t B) {
   if (!c || B < 1) return 0;
@@ -635,6 +657,70 @@ ephdc_status bfv_ptct_similarity(ephdc_ctx* c, const uint32_t* pt, int32_t B, co
   if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
   CHECK_B(c, B);
   return similarity_impl(c, pt, B, model, gk, out, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ seeded model message
+ephdc_status bfv_model_to_seeded(ephdc_ctx* c, const void* model, uint32_t* seeded,
+                                 void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, model, "model_dev");
+  CHECK_PTR(c, seeded, "seeded_dev");
+  return launched(c, ephdc::launch_model_to_seeded(c->dc, (const uint32_t*)model, seeded,
+                                                   (cudaStream_t)stream),
+                  "model_to_seeded");
+}
+
+ephdc_status bfv_model_from_seeded(ephdc_ctx* c, const uint32_t* seeded, uint64_t seed,
+                                   void* model, void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, seeded, "seeded_dev");
+  CHECK_PTR(c, model, "model_dev");
+  return launched(c, ephdc::launch_model_from_seeded(c->dc, seeded, seed, (uint32_t*)model,
+                                                     (cudaStream_t)stream),
+                  "model_from_seeded");
+}
+
+// ------------------------------------------------------------------ noise growth
+ephdc_status ephdc_find_dmax_trial(ephdc_ctx* c, const void* sk, const int8_t* H, int32_t B,
+                                   const int8_t* classes, const uint32_t* pt, const void* model,
+                                   int32_t* dmax) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, sk, "sk_dev");
+  CHECK_PTR(c, H, "H_dev");
+  CHECK_PTR(c, classes, "class_hv_dev");
+  CHECK_PTR(c, pt, "pt_dev");
+  CHECK_PTR(c, model, "model_dev");
+  if (!dmax) return fail(c, EPHDC_EINVAL, "dmax is NULL");
+  const DevCtx& d = c->dc;
+  if (d.k != 1 || d.k_in != 1 || d.r != 1)
+    return fail(c, EPHDC_EUNSUPPORTED, "needs one class and the layout k_in = 1, r = 1");
+  if (B < 1 || (uint32_t)B > d.cap || (uint32_t)B > c->prm.max_batch)
+    return fail(c, EPHDC_EINVAL, "B must be in [1, min(cap, max_batch)]");
+  const int D = (int)d.D;
+  const size_t ln = (size_t)d.L * d.n;
+  const size_t xw = (size_t)D * ln, tw = (size_t)ephdc::prefix_chunks(d, D) * ln;
+  const size_t sw = (size_t)D * d.cap;
+  uint8_t* buf = nullptr;
+  const size_t bytes = (xw + tw + sw) * sizeof(uint32_t) + 256;
+  if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, EPHDC_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+  }
+  uint32_t* X = (uint32_t*)buf;
+  uint32_t* T = X + xw;
+  uint32_t* scores = T + tw;
+  int* first = (int*)(scores + sw);
+  cudaError_t e = cudaMemcpy(first, &D, sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = ephdc::launch_prefix_phases(d, pt, (const uint32_t*)model, (const uint32_t*)sk, D, X, T, 0);
+  if (e == cudaSuccess) e = ephdc::launch_decrypt_phases(d, X, D, D * (int)d.cap, scores, 0);
+  if (e == cudaSuccess) e = ephdc::launch_first_wrong(d, H, classes, B, D, scores, first, 0);
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, first, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_status(c, e, "find_dmax_trial");
+  *dmax = v;
+  return EPHDC_OK;
 }
 
 // ------------------------------------------------------------------ server-side variant

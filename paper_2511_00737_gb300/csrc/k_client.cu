@@ -41,18 +41,31 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
   pack_query_slots(c, H, B, g, i, mb);
   __syncthreads();
   ntt_inv_t<LOGN, V>(mb, c.mt);  // slots -> coefficients in [0, t)
-  constexpr uint32_t thalf = (EPHDC_T - 1) / 2;
+  const uint32_t t = c.t, thalf = (t - 1) / 2;
   for (uint32_t l = 0; l < c.L; l++) {
-    const uint32_t p = c.mq[l].p;
+    const ModP m = c.mq[l];
+    const uint32_t p = m.p;
     auto lift = [=](uint32_t k) -> uint32_t {
       const uint32_t v = mb[padi(k)];
-      return v <= thalf ? v : v + p - EPHDC_T;  // centred lift into Z_{q_l}
+      return v <= thalf ? v : v + p - t;  // centred lift into Z_{q_l}
     };
-    ntt_fwd_io<LOGN, decltype(lift), SmemSt, V>(wb, c.mq[l], lift, SmemSt{wb});
+    ntt_fwd_io<LOGN, decltype(lift), SmemSt, V>(wb, m, lift, SmemSt{wb});
     uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
-    for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
-      dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
-                          wb[padi(4 * k + 3)]);
+    if (c.scale_g == 0) {
+      for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
+        dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
+                            wb[padi(4 * k + 3)]);
+    } else {
+      // scaling operation folded into the plaintext: the accumulator scaled after
+      // every g products equals, mod q_l, the sum of the products with plaintext i
+      // multiplied by w^(floor(P/g) - floor(i/g))
+      const uint32_t w = scale_factor(c, l, c.P / c.scale_g - i / c.scale_g);
+      const uint32_t wsh = (uint32_t)(((uint64_t)w << 32) / p);
+      auto sc = [=](uint32_t v) { return csub(mulshoup(v, w, wsh, p), p); };
+      for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
+        dst[k] = make_uint4(sc(wb[padi(4 * k)]), sc(wb[padi(4 * k + 1)]),
+                            sc(wb[padi(4 * k + 2)]), sc(wb[padi(4 * k + 3)]));
+    }
     __syncthreads();
   }
 }

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(512) k_galois_keys(DevCtx c, uint64_t seed,
 // ------------------------------------------------------------------ model encryption
 // One CTA per (ciphertext i*Kp + jp, limb l).  Class value c_{jp*k_in+jin}[i*r+ch] fills
 // slot (rho, ch*W + jin*cap_row + qq) for all qq < cap_row; encode with the inverse NTT
-// mod t; c1 = a, c0 = -a s + e + floor(q/t) m.
+// mod t; c1 = a, c0 = -a s + e + round(q m / t).
 __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* __restrict__ cls,
                                                        const uint32_t* __restrict__ sk,
                                                        uint64_t seed, uint32_t* __restrict__ model) {
@@ -99,27 +99,57 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
     const uint32_t d = i * c.r + ch;
     if (jin < c.k_in && d < c.D) {
       const int h = cls[(size_t)(jp * c.k_in + jin) * c.D + d];
-      v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
+      v = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
     }
     mb[padi(x)] = v;
   }
   fill_uniform(c, seed, 2, cidx, l, ab);
   fill_gauss(c, seed, 3, cidx, m.p, eb);
   __syncthreads();
-  ntt_inv_smem(mb, c.logn, c.mt);  // m in [0, t), a valid residue mod q_l as is
+  ntt_inv_smem(mb, c.logn, c.mt);  // m in [0, t)
+  // the scaled message round(q m / t) is formed per coefficient (it is not linear in
+  // m), then transformed with a and e
+  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x)
+    mb[padi(x)] = scaled_msg(c, l, mb[padi(x)]);
+  __syncthreads();
   ntt_fwd_smem(mb, c.logn, m);
   ntt_fwd_smem(ab, c.logn, m);
   ntt_fwd_smem(eb, c.logn, m);
   const uint32_t* s = sk + (size_t)l * c.n;
   uint32_t* c0 = model + ((size_t)(cidx * 2 + 0) * c.L + l) * c.n;
   uint32_t* c1 = model + ((size_t)(cidx * 2 + 1) * c.L + l) * c.n;
-  const uint32_t dl = c.delta[l];
   for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) {
     const uint32_t a = ab[padi(x)];
     uint32_t v = subm(eb[padi(x)], mulm(a, s[x], m), m.p);
-    v = addm(v, mulm(dl, mb[padi(x)], m), m.p);
-    c0[x] = v;
+    c0[x] = addm(v, mb[padi(x)], m.p);
     c1[x] = a;
+  }
+}
+
+// ------------------------------------------------------------------ seeded model message
+// One CTA per (model ciphertext, limb): c0 from the coefficient-domain message into the
+// NTT domain, and c1 = a regenerated from the ChaCha20 stream the encryption drew it
+// from (domain 2, ciphertext number), then transformed.
+__global__ void __launch_bounds__(512) k_model_from_seeded(DevCtx c,
+                                                           const uint32_t* __restrict__ c0w,
+                                                           uint64_t seed,
+                                                           uint32_t* __restrict__ model) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* b0 = sm;
+  uint32_t* b1 = sm + padded_words(c.n);
+  const uint32_t cidx = blockIdx.x, l = blockIdx.y;
+  const ModP m = c.mq[l];
+  const uint32_t* src = c0w + ((size_t)cidx * c.L + l) * c.n;
+  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) b0[padi(x)] = src[x];
+  fill_uniform(c, seed, 2, cidx, l, b1);
+  __syncthreads();
+  ntt_fwd_smem(b0, c.logn, m);
+  ntt_fwd_smem(b1, c.logn, m);
+  uint32_t* c0 = model + ((size_t)(cidx * 2 + 0) * c.L + l) * c.n;
+  uint32_t* c1 = model + ((size_t)(cidx * 2 + 1) * c.L + l) * c.n;
+  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) {
+    c0[x] = b0[padi(x)];
+    c1[x] = b1[padi(x)];
   }
 }
 
@@ -193,16 +223,16 @@ __global__ void __launch_bounds__(512) k_dec_scores(DevCtx c, const uint32_t* __
       big_add(X, term);
     }
     while (big_ge(X, c.big_Q)) big_sub(X, c.big_Q);
-    // num = t X + floor(Q/2); quotient bit by bit (< 2^18)
+    // num = t X + floor(Q/2); quotient bit by bit (it is at most t)
     uint64_t cr = 0;
     for (int w = 0; w < EPHDC_BIGW; w++) {
-      uint64_t v = (uint64_t)X[w] * EPHDC_T + cr;
+      uint64_t v = (uint64_t)X[w] * c.t + cr;
       X[w] = (uint32_t)v;
       cr = v >> 32;
     }
     big_add(X, c.big_Qhalf);
     uint32_t quo = 0;
-    for (int b = 17; b >= 0; b--) {
+    for (int b = 31 - __clz(c.t); b >= 0; b--) {
       uint32_t Qs[EPHDC_BIGW];
       for (int w = 0; w < EPHDC_BIGW; w++) {
         uint64_t v = ((uint64_t)c.big_Q[w] << b);
@@ -215,7 +245,7 @@ __global__ void __launch_bounds__(512) k_dec_scores(DevCtx c, const uint32_t* __
         quo |= 1u << b;
       }
     }
-    sm[padi(x)] = quo % EPHDC_T;
+    sm[padi(x)] = quo % c.t;
   }
   __syncthreads();
   ntt_fwd_smem(sm, c.logn, c.mt);  // coefficients -> slots (device order)
@@ -311,6 +341,31 @@ cudaError_t launch_decrypt_scores(const DevCtx& c, const uint32_t* sk, const uin
   if (e == cudaSuccess) e = set_smem(k_dec_scores, s1);
   if (e != cudaSuccess) return e;
   k_dec_phase<<<dim3(count, c.L), ntt_threads(c), s2, st>>>(c, ct, sk, xbuf);
+  k_dec_scores<<<count, ntt_threads(c), s1, st>>>(c, xbuf, B, scores);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_model_to_seeded(const DevCtx& c, const uint32_t* model, uint32_t* c0w,
+                                  cudaStream_t st) {
+  // c0 of every model ciphertext ([P*Kp][2][L][n], NTT domain) to [P*Kp][L][n] coefficients
+  return launch_to_coeff(c, model, c0w, (int)(c.P * c.Kp), 1, (int)(2 * c.L * c.n), (int)c.n, 0,
+                         st);
+}
+
+cudaError_t launch_model_from_seeded(const DevCtx& c, const uint32_t* c0w, uint64_t seed,
+                                    uint32_t* model, cudaStream_t st) {
+  const size_t smem = 2 * padded_words(c.n) * 4;
+  cudaError_t e = set_smem(k_model_from_seeded, smem);
+  if (e != cudaSuccess) return e;
+  k_model_from_seeded<<<dim3(c.P * c.Kp, c.L), ntt_threads(c), smem, st>>>(c, c0w, seed, model);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decrypt_phases(const DevCtx& c, const uint32_t* xbuf, int count, int B,
+                                  uint32_t* scores, cudaStream_t st) {
+  const size_t s1 = padded_words(c.n) * 4;
+  cudaError_t e = set_smem(k_dec_scores, s1);
+  if (e != cudaSuccess) return e;
   k_dec_scores<<<count, ntt_threads(c), s1, st>>>(c, xbuf, B, scores);
   return cudaGetLastError();
 }

@@ -23,8 +23,8 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 // ------------------------------------------------------------------ query encryption
 // One CTA per query ciphertext (g, i): the slots of query plaintext (g, i) are packed
 // as in the client-side encoder, the inverse NTT mod t gives m in [0, t), and per limb
-//   c0 = NTT(Delta m + e) - NTT(a) * s,   c1 = NTT(a)
-// (the NTT is linear, so NTT(Delta m + e) is one transform).  e (|e| <= 19) is drawn
+//   c0 = NTT(round(Q m / t) + e) - NTT(a) * s,   c1 = NTT(a)
+// (the NTT is linear, so NTT(round(Q m / t) + e) is one transform).  e (|e| <= 19) is drawn
 // once and kept as bytes; both transforms of a limb finish in shared memory and the
 // ciphertext is written with 16-byte stores.
 template <int LOGN, int V>
@@ -54,10 +54,11 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 2)
   ntt_inv_t<LOGN, V>(mb, c.mt);  // slots -> m in [0, t)
   for (uint32_t l = 0; l < c.L; l++) {
     const ModP m = c.mq[l];
-    const uint32_t p = m.p, dl = c.delta[l];
+    const uint32_t p = m.p;
     auto dm_e = [=](uint32_t k) -> uint32_t {
       const int32_t e = eb[k];
-      return addm(mulm(dl, mb[padi(k)], m), e < 0 ? (uint32_t)((int32_t)p + e) : (uint32_t)e, p);
+      return addm(scaled_msg(c, l, mb[padi(k)]), e < 0 ? (uint32_t)((int32_t)p + e) : (uint32_t)e,
+                  p);
     };
     ntt_fwd_io<LOGN, decltype(dm_e), SmemSt, V>(wb, m, dm_e, SmemSt{vb});
     fill_uniform(c, seed, 6, gi, l, wb);
@@ -106,23 +107,27 @@ __global__ void __launch_bounds__(512) k_encode_model_plain(DevCtx c,
     const uint32_t d = i * c.r + ch;
     if (jin < c.k_in && d < c.D) {
       const int h = cls[(size_t)(jp * c.k_in + jin) * c.D + d];
-      v = h < 0 ? (uint32_t)(h + (int)EPHDC_T) : (uint32_t)h;
+      v = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
     }
     mb[padi(x)] = v;
   }
   __syncthreads();
   ntt_inv_smem(mb, c.logn, c.mt);
-  constexpr uint32_t thalf = (EPHDC_T - 1) / 2;
+  const uint32_t t = c.t, thalf = (t - 1) / 2;
   for (uint32_t l = 0; l < c.L; l++) {
-    const uint32_t p = c.mq[l].p;
+    const ModP m = c.mq[l];
+    const uint32_t p = m.p;
     for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) {
       const uint32_t v = mb[padi(x)];
-      wb[padi(x)] = v <= thalf ? v : v + p - EPHDC_T;
+      wb[padi(x)] = v <= thalf ? v : v + p - t;
     }
     __syncthreads();
-    ntt_fwd_smem(wb, c.logn, c.mq[l]);
+    ntt_fwd_smem(wb, c.logn, m);
+    // the scaling operation folded into plaintext i (as on the client-side path)
+    const uint32_t w = c.scale_g ? scale_factor(c, l, c.P / c.scale_g - i / c.scale_g) : 1;
     uint32_t* dst = mm + ((size_t)cidx * c.L + l) * c.n;
-    for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) dst[x] = wb[padi(x)];
+    for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x)
+      dst[x] = w == 1 ? wb[padi(x)] : mulm(wb[padi(x)], w, m);
     __syncthreads();
   }
 }

@@ -34,7 +34,9 @@ class ephdc_params(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("L", ctypes.c_uint32), ("k", ctypes.c_uint32),
                 ("k_in", ctypes.c_uint32), ("r", ctypes.c_uint32), ("D", ctypes.c_uint32),
                 ("F", ctypes.c_uint32), ("hv_bits", ctypes.c_uint32), ("shift", ctypes.c_int32),
-                ("max_batch", ctypes.c_uint32), ("sigma", ctypes.c_double)]
+                ("max_batch", ctypes.c_uint32), ("sigma", ctypes.c_double),
+                ("t", ctypes.c_uint32), ("prime_bits", ctypes.c_uint32),
+                ("scale_shift", ctypes.c_uint32), ("scale_group", ctypes.c_uint32)]
 
 
 _LIB = None
@@ -76,6 +78,11 @@ _SIGS = {
                                            _VP]),
     "bfv_encode_model_plain": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "bfv_ctpt_similarity": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
+    "ephdc_measure_int_peaks": (ctypes.c_int, [_VP, _VP]),
+    "ephdc_find_dmax_trial": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
+    "ephdc_model_seeded_bytes": (ctypes.c_size_t, [_VP]),
+    "bfv_model_to_seeded": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "bfv_model_from_seeded": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, _VP, _VP]),
 }
 
 STAGES = ["hdc_encode", "encode_plain", "mac", "rotate", "export", "encrypt_queries"]
@@ -132,8 +139,10 @@ def _check(ctx, status):
 
 
 # ------------------------------------------------------------------ C names
-def ephdc_ctx_create(n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma=3.2):
-    p = ephdc_params(n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma)
+def ephdc_ctx_create(n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma=3.2, t=0,
+                     prime_bits=0, scale_shift=0, scale_group=0):
+    p = ephdc_params(n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma, t, prime_bits,
+                     scale_shift, scale_group)
     out = _VP()
     st = lib().ephdc_ctx_create(ctypes.byref(p), ctypes.byref(out))
     _check(None, st)
@@ -219,20 +228,39 @@ def bfv_ctpt_similarity(ctx, query_ct, B, model_plain, gk, out_ct, stream=None):
                                           _ptr(out_ct, "out_ct"), _stream(stream)))
 
 
+def ephdc_find_dmax_trial(ctx, sk, H, classes, pt, model):
+    """Largest D' <= D whose evaluations with 1..D' dimensions all decrypt correctly."""
+    out = ctypes.c_int32(0)
+    _check(ctx, lib().ephdc_find_dmax_trial(ctx, _ptr(sk, "sk"), _ptr(H, "H", dtype=torch.int8),
+                                            H.shape[0], _ptr(classes, "classes", dtype=torch.int8),
+                                            _ptr(pt, "pt"), _ptr(model, "model"),
+                                            ctypes.byref(out)))
+    return out.value
+
+
+def ephdc_measure_int_peaks():
+    """(butterflies/s, 64-bit multiply-accumulates/s) of the current device."""
+    b, m = ctypes.c_double(0), ctypes.c_double(0)
+    _check(None, lib().ephdc_measure_int_peaks(ctypes.byref(b), ctypes.byref(m)))
+    return b.value, m.value
+
+
 # ------------------------------------------------------------------ convenience
 class Context:
     """One set of BFV parameters + slot layout; allocates correctly sized tensors."""
 
     def __init__(self, n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma=3.2,
-                 device=None):
+                 device=None, t=0, prime_bits=0, scale_shift=0, scale_group=0):
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
-            self.ctx = ephdc_ctx_create(n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma)
+            self.ctx = ephdc_ctx_create(n, L, k, k_in, r, D, F, hv_bits, shift, max_batch, sigma,
+                                        t, prime_bits, scale_shift, scale_group)
         self.n, self.L, self.k, self.k_in, self.r, self.D, self.F = n, L, k, k_in, r, D, F
         self.hv_bits, self.shift, self.max_batch = hv_bits, shift, max_batch
         q = lambda w: int(lib().ephdc_query(self.ctx, w.encode()))
         self.cap, self.P, self.Kp, self.W, self.logr = q("cap"), q("P"), q("Kp"), q("W"), q("logr")
         self.q = [q("q%d" % l) for l in range(L)]
+        self.t = q("t")
 
     @classmethod
     def for_workload(cls, w, max_batch=None):
@@ -301,6 +329,19 @@ class Context:
         out = self.out_ct(B) if out is None else out
         ephdc_infer(self.ctx, X, Wt, B, model, gk, out, stream)
         return out
+
+    # seeded model message (c0 + seed)
+    def model_to_seeded(self, model, stream=None):
+        out = self._u32(lib().ephdc_model_seeded_bytes(self.ctx))
+        _check(self.ctx, lib().bfv_model_to_seeded(self.ctx, _ptr(model, "model"),
+                                                   _ptr(out, "seeded"), _stream(stream)))
+        return out
+
+    def model_from_seeded(self, seeded, seed, stream=None):
+        model = self._u32(lib().ephdc_model_bytes(self.ctx))
+        _check(self.ctx, lib().bfv_model_from_seeded(self.ctx, _ptr(seeded, "seeded"), seed,
+                                                     _ptr(model, "model"), _stream(stream)))
+        return model
 
     # server-side variant
     def encrypt_queries(self, H, sk, seed, out=None, stream=None):
