@@ -47,6 +47,8 @@ def parse():
                     help="streams (contexts) that consecutive batches alternate over")
     ap.add_argument("--mac-mode", type=int, default=-1,
                     help="force the multiply-accumulate schedule (profiling)")
+    ap.add_argument("--pack", type=int, default=1,
+                    help="consecutive batches packed into one step (one model stream)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
     return ap.parse_args()
@@ -181,11 +183,11 @@ def run_reference(args, w, B):
     print(json.dumps(line), flush=True)
 
 
-def config_of(w, B):
+def config_of(w, B, per_step=None):
     return {"workload": "%s: B=%d queries, F=%d, D=%d, %d-bit HVs, k=%d classes, BFV n=%d, "
                         "t=65537, L=%d x 30-bit primes, layout k_in=%d r=%d" % (
                             w.name, B, w.F, w.D, w.bits, w.k, w.n, w.L, w.k_in, w.r),
-            "global_batch": B, "n": w.n, "L": w.L, "D": w.D, "F": w.F, "k": w.k,
+            "global_batch": per_step or B, "n": w.n, "L": w.L, "D": w.D, "F": w.F, "k": w.k,
             "hv_bits": w.bits, "k_in": w.k_in, "r": w.r,
             "l2": "inputs larger than L2: the encrypted model streamed every step is "
                   "larger than the 129 MB L2", "parallelism": "replicas"}
@@ -208,6 +210,10 @@ def run_ours(args, w, B):
     seed = w.seed + 7919 * rank
     multi = bool(w.clients)
     cap = 2 * ((w.n // (2 * w.r)) // w.k_in)
+    # a step packs `pack` consecutive batches of the workload into one pass, so the
+    # encrypted model is streamed once for all of their groups
+    batch, pack = B, (1 if multi else max(1, args.pack))
+    B = batch * pack
     if multi:
         from paper_2511_00737_gb300 import autotune as AT
         from paper_2511_00737_gb300 import batching as BT
@@ -387,7 +393,7 @@ def run_ours(args, w, B):
     # client runtime against the server-side variant, on one batch of at most 4 groups
     clrt = None
     if not args.no_sr and rank == 0 and not multi:
-        clrt = client_runtime(w, dev, min(B, 4 * cap))
+        clrt = client_runtime(w, dev, min(batch, 4 * cap))
 
     # roofline of the dominant stage
     pk, src = peaks()
@@ -400,19 +406,21 @@ def run_ours(args, w, B):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, B, args.cpu_budget_s, seed)
+        cpu = cpu_baseline(w, batch, args.cpu_budget_s, seed)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "u32", "data": "synthetic", "config": config_of(w, B),
+                "dtype": "u32", "data": "synthetic", "config": config_of(w, batch, B),
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "roofline": roof, "cpu_baseline": cpu,
                 "stages_ms_per_step": {k: v / max(1, args.steps) for k, v in stage_ms.items()},
                 "per_query_form": perq, "client_runtime_vs_server_side": clrt}
         if not multi:
             line["config"]["streams"] = S
+            line["config"]["batches_per_step"] = pack
+            line["config"]["batch"] = batch
         if not multi and tuned:
             line["config"]["mac_schedule"] = tuned
         if multi:

@@ -67,8 +67,8 @@ typedef struct {
   int32_t shift;      /* quantiser shift s >= 0                                   */
   uint32_t max_batch; /* largest batch B any call on this context will use        */
   double sigma;       /* error standard deviation (3.2)                           */
-  uint32_t t;         /* plaintext modulus: a prime = 1 (mod 2n) below 2^30;
-                         0 selects 65537                                           */
+  uint32_t t;         /* plaintext modulus: a prime = 1 (mod 2n) below the smallest
+                         RNS prime; 0 selects 65537                                */
   uint32_t prime_bits;/* the L RNS primes are the largest primes below 2^prime_bits
                          with q = 1 (mod 2n); 20..30, 0 selects 30                 */
   uint32_t scale_shift; /* scaling operation of Sec. 5.1: 0 = off; else the running

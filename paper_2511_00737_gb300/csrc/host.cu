@@ -251,6 +251,13 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
     if (prime32((uint32_t)cand)) q.push_back((uint32_t)cand);
   }
 
+  // the centred lift of plaintext coefficients (|v| <= t/2) into Z_{q_l} and the
+  // scaled-message arithmetic take t below every RNS prime
+  if (t >= q.back()) {
+    delete c;
+    return fail(nullptr, EPHDC_EINVAL, "t = %u must be below the smallest RNS prime %u", t,
+                q.back());
+  }
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
     return fail(nullptr, EPHDC_ECUDA, "no CUDA device");

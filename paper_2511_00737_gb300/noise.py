@@ -63,7 +63,8 @@ def plaintext_modulus(n, log_t):
 
 
 def rns_at_bound(n, prime_bits=27):
-    """(L, prime_bits) with L primes of prime_bits bits inside the 128-bit bound."""
+    """(L, prime_bits) with L primes of prime_bits bits inside the 128-bit bound.
+    The plaintext modulus must stay below the primes (log2 t < prime_bits)."""
     return max(2, min(8, LOGQ_128[n] // prime_bits)), prime_bits
 
 
@@ -106,6 +107,8 @@ def find_dmax(n, log_t, trials, L=None, prime_bits=27, d_lim=None, seed=1, d_cap
     if L is None:
         L, prime_bits = rns_at_bound(n, prime_bits)
     t = plaintext_modulus(n, log_t)
+    if t >= (1 << (prime_bits - 1)):
+        raise ValueError("t = %d is not below the %d-bit primes" % (t, prime_bits))
     t0 = time.time()
     if d_lim is None:
         d_lim = 64

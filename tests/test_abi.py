@@ -44,7 +44,8 @@ def test_invalid_parameters_rejected_on_host():
     for bad in [dict(n=1000), dict(L=1), dict(k=3, k_in=2), dict(r=3), dict(F=100),
                 dict(hv_bits=9), dict(max_batch=0), dict(r=4096),
                 dict(t=65539), dict(t=40961 * 3), dict(t=786433 * 2048 + 1),
-                dict(prime_bits=31), dict(prime_bits=12), dict(scale_shift=31)]:
+                dict(prime_bits=31), dict(prime_bits=12), dict(scale_shift=31),
+                dict(t=536903681, prime_bits=27)]:
         p = dict(n=4096, L=3, k=2, k_in=2, r=8, D=100, F=64, hv_bits=4, shift=3, max_batch=16,
                  sigma=3.2)
         p.update(bad)
