@@ -170,23 +170,30 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
   const uint64_t mu = c.mq[l].mu;
   const size_t n = c.n, L = c.L, P = c.P;
 
+  // copy slots: slot q = rr * 8 + piece (row rr of a staged plaintext index, 16-byte
+  // piece, shared-memory word offset 4 q) belongs to thread q mod blockDim for every
+  // plaintext of a chunk, so its source address is formed once per chunk and advanced
+  // by a fixed stride; rows * 8 <= 4 * blockDim is checked by the launcher
+  const size_t pt_stride = L * n, model_stride = (size_t)O * L * n;
   auto load_chunk = [&](int b, uint32_t i0) {
     uint32_t* dst = sm + b * buf_words;
-    const int copies = IC * rows * 8;  // 16-byte pieces
-    for (int t = threadIdx.x; t < copies; t += blockDim.x) {
-      const int piece = t & 7, row = t >> 3;
-      const int ii = row / rows, rr = row - ii * rows;
-      const uint32_t i = i0 + ii;
-      const uint32_t* src;
-      bool ok = i < P;
-      if (rr < GC) {  // plaintext of group g0 + rr
-        const int g = g0 + rr;
-        ok = ok && g < G;
-        src = pt + (((size_t)(ok ? g : 0) * P + (ok ? i : 0)) * L + l) * n + k0 + piece * 4;
-      } else {        // model ciphertext output rr - GC
-        src = model + (((size_t)(ok ? i : 0) * O + (rr - GC)) * L + l) * n + k0 + piece * 4;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int q = threadIdx.x + k * blockDim.x;
+      if (q < rows * 8) {
+        const int rr = q >> 3, piece = q & 7;
+        const bool is_pt = rr < GC;
+        const bool gok = !is_pt || g0 + rr < G;
+        const size_t stride = is_pt ? pt_stride : model_stride;
+        const uint32_t* src =
+            is_pt ? pt + ((size_t)(gok ? g0 + rr : 0) * P * L + l) * n + k0 + piece * 4
+                  : model + ((size_t)(rr - GC) * L + l) * n + k0 + piece * 4;
+        src += (size_t)i0 * stride;
+        for (int ii = 0; ii < IC; ii++, src += stride) {
+          const bool ok = gok && i0 + ii < P;
+          cp_async16_zfill(dst + ii * rows * 32 + 4 * q, ok ? src : pt, ok);
+        }
       }
-      cp_async16_zfill(dst + row * 32 + piece * 4, src, ok);
     }
     asm volatile("cp.async.commit_group;\n");
   };
@@ -392,7 +399,8 @@ static cudaError_t run_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, con
   if (IC > 15) IC = 15;
   const int warps = (GC / GT) * ((O + OT - 1) / OT);
   const size_t smem = 2 * (size_t)IC * (GC + O) * 32 * sizeof(uint32_t);
-  if (warps < 1 || warps > 16 || GC % GT) return cudaErrorInvalidConfiguration;
+  if (warps < 1 || warps > 16 || GC % GT || (GC + O) * 8 > 4 * warps * 32)
+    return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_mac_tiled<GT, OT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
