@@ -597,7 +597,7 @@ int prefix_chunks(const DevCtx& c, int D);
 cudaError_t launch_prefix_phases(const DevCtx& c, const uint32_t* pt, const uint32_t* model,
                                  const uint32_t* sk, int D, uint32_t* X, uint32_t* T,
                                  cudaStream_t st);
-cudaError_t launch_decrypt_phases(const DevCtx& c, const uint32_t* xbuf, int count, int B,
+cudaError_t launch_decrypt_phases(const DevCtx& c, uint32_t* xbuf, int count, int B,
                                   uint32_t* scores, cudaStream_t st);
 cudaError_t launch_first_wrong(const DevCtx& c, const int8_t* H, const int8_t* cls, int B, int D,
                                const uint32_t* scores, int* first, cudaStream_t st);

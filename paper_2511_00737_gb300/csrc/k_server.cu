@@ -202,51 +202,60 @@ __device__ void big_sub(uint32_t* a, const uint32_t* b) {
   }
 }
 
-// one CTA per score ciphertext: CRT + round(t x / Q) mod t, encode back to slots with
-// the forward NTT mod t, then read the score slots
+// one thread per coefficient of each score ciphertext: CRT of the phase limbs, then
+// round(t x / Q) mod t, written over limb 0 of the coefficient (only this thread reads
+// that coefficient's limbs)
+__global__ void __launch_bounds__(256) k_dec_round(DevCtx c, uint32_t* __restrict__ xbuf) {
+  const uint32_t item = blockIdx.x;
+  const uint32_t x = blockIdx.y * blockDim.x + threadIdx.x;
+  if (x >= c.n) return;
+  uint32_t X[EPHDC_BIGW] = {0};
+  for (uint32_t l = 0; l < c.L; l++) {
+    const uint32_t y = mulm(xbuf[((size_t)item * c.L + l) * c.n + x], c.qhat_inv[l], c.mq[l]);
+    uint32_t term[EPHDC_BIGW];
+    uint64_t cr = 0;
+    for (int w = 0; w < EPHDC_BIGW; w++) {
+      uint64_t v = (uint64_t)c.big_Qhat[l][w] * y + cr;
+      term[w] = (uint32_t)v;
+      cr = v >> 32;
+    }
+    big_add(X, term);
+  }
+  while (big_ge(X, c.big_Q)) big_sub(X, c.big_Q);
+  // num = t X + floor(Q/2); quotient bit by bit (it is at most t)
+  uint64_t cr = 0;
+  for (int w = 0; w < EPHDC_BIGW; w++) {
+    uint64_t v = (uint64_t)X[w] * c.t + cr;
+    X[w] = (uint32_t)v;
+    cr = v >> 32;
+  }
+  big_add(X, c.big_Qhalf);
+  uint32_t quo = 0;
+  for (int b = 31 - __clz(c.t); b >= 0; b--) {
+    uint32_t Qs[EPHDC_BIGW];
+    for (int w = 0; w < EPHDC_BIGW; w++) {
+      uint64_t v = ((uint64_t)c.big_Q[w] << b);
+      uint32_t lo = (uint32_t)v;
+      uint32_t carry_in = (w > 0 && b > 0) ? (c.big_Q[w - 1] >> (32 - b)) : 0;
+      Qs[w] = lo | carry_in;
+    }
+    if (big_ge(X, Qs)) {
+      big_sub(X, Qs);
+      quo |= 1u << b;
+    }
+  }
+  xbuf[(size_t)item * c.L * c.n + x] = quo % c.t;
+}
+
+// one CTA per score ciphertext: the rounded coefficients back to slots with the
+// forward NTT mod t, then the score slots
 __global__ void __launch_bounds__(512) k_dec_scores(DevCtx c, const uint32_t* __restrict__ xbuf,
                                                     int B, uint32_t* __restrict__ scores) {
   extern __shared__ uint32_t sm[];
   const uint32_t item = blockIdx.x;
   const uint32_t g = item / c.Kp, jp = item - g * c.Kp;
-  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) {
-    uint32_t X[EPHDC_BIGW] = {0};
-    for (uint32_t l = 0; l < c.L; l++) {
-      const uint32_t y = mulm(xbuf[((size_t)item * c.L + l) * c.n + x], c.qhat_inv[l], c.mq[l]);
-      uint32_t term[EPHDC_BIGW];
-      uint64_t cr = 0;
-      for (int w = 0; w < EPHDC_BIGW; w++) {
-        uint64_t v = (uint64_t)c.big_Qhat[l][w] * y + cr;
-        term[w] = (uint32_t)v;
-        cr = v >> 32;
-      }
-      big_add(X, term);
-    }
-    while (big_ge(X, c.big_Q)) big_sub(X, c.big_Q);
-    // num = t X + floor(Q/2); quotient bit by bit (it is at most t)
-    uint64_t cr = 0;
-    for (int w = 0; w < EPHDC_BIGW; w++) {
-      uint64_t v = (uint64_t)X[w] * c.t + cr;
-      X[w] = (uint32_t)v;
-      cr = v >> 32;
-    }
-    big_add(X, c.big_Qhalf);
-    uint32_t quo = 0;
-    for (int b = 31 - __clz(c.t); b >= 0; b--) {
-      uint32_t Qs[EPHDC_BIGW];
-      for (int w = 0; w < EPHDC_BIGW; w++) {
-        uint64_t v = ((uint64_t)c.big_Q[w] << b);
-        uint32_t lo = (uint32_t)v;
-        uint32_t carry_in = (w > 0 && b > 0) ? (c.big_Q[w - 1] >> (32 - b)) : 0;
-        Qs[w] = lo | carry_in;
-      }
-      if (big_ge(X, Qs)) {
-        big_sub(X, Qs);
-        quo |= 1u << b;
-      }
-    }
-    sm[padi(x)] = quo % c.t;
-  }
+  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x)
+    sm[padi(x)] = xbuf[(size_t)item * c.L * c.n + x];
   __syncthreads();
   ntt_fwd_smem(sm, c.logn, c.mt);  // coefficients -> slots (device order)
   const uint32_t half = c.n >> 1;
@@ -341,6 +350,7 @@ cudaError_t launch_decrypt_scores(const DevCtx& c, const uint32_t* sk, const uin
   if (e == cudaSuccess) e = set_smem(k_dec_scores, s1);
   if (e != cudaSuccess) return e;
   k_dec_phase<<<dim3(count, c.L), ntt_threads(c), s2, st>>>(c, ct, sk, xbuf);
+  k_dec_round<<<dim3(count, (c.n + 255) / 256), 256, 0, st>>>(c, xbuf);
   k_dec_scores<<<count, ntt_threads(c), s1, st>>>(c, xbuf, B, scores);
   return cudaGetLastError();
 }
@@ -361,11 +371,12 @@ cudaError_t launch_model_from_seeded(const DevCtx& c, const uint32_t* c0w, uint6
   return cudaGetLastError();
 }
 
-cudaError_t launch_decrypt_phases(const DevCtx& c, const uint32_t* xbuf, int count, int B,
+cudaError_t launch_decrypt_phases(const DevCtx& c, uint32_t* xbuf, int count, int B,
                                   uint32_t* scores, cudaStream_t st) {
   const size_t s1 = padded_words(c.n) * 4;
   cudaError_t e = set_smem(k_dec_scores, s1);
   if (e != cudaSuccess) return e;
+  k_dec_round<<<dim3(count, (c.n + 255) / 256), 256, 0, st>>>(c, xbuf);
   k_dec_scores<<<count, ntt_threads(c), s1, st>>>(c, xbuf, B, scores);
   return cudaGetLastError();
 }
