@@ -528,6 +528,12 @@ def per_query_form(w, dev, queries=32):
             "layout": "k_in=%d r=%d (%d rotations per query)" % (kin, r, int(math.log2(r)))}
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
+# the same kernel and launch shape (dram__bytes_read.sum + dram__bytes_write.sum):
+# (workload, groups per launch, stage) -> bytes
+NCU_TRAFFIC = {("face1024", 8, "encode_plain"): 1332334592}
+
+
 def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
     G = ctx.groups(B)
     P, Kp, L, n = ctx.P, ctx.Kp, ctx.L, ctx.n
@@ -560,7 +566,8 @@ def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
         peak = pk["bfly_tps"]
         return {"kernel": "encode_plain", "bound": "alu", "achieved": ach,
                 "peak": peak, "unit": "Tbutterfly/s", "frac": ach / peak,
-                "traffic": None,
+                "traffic": NCU_TRAFFIC.get((w.name, G, "encode_plain")),
+                "algorithmic_bytes": B * w.D + G * P * L * n * 4,
                 "peak_source": "measured: register-only lazy Shoup butterflies "
                                "(ephdc_measure_int_peaks); issue-limit estimate %.2f" %
                                alu_peak_tbfly(pk),
