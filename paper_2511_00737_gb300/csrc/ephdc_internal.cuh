@@ -85,11 +85,12 @@ __device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, const ModP& m) 
 
 // scale_w[l]^e mod q_l (square and multiply; e is at most P)
 __device__ __forceinline__ uint32_t scale_factor(const DevCtx& c, uint32_t l, uint32_t e) {
-  const ModP& m = c.mq[l];
+  const uint32_t p = c.mq[l].p;
+  const uint64_t mu = c.mq[l].mu;
   uint32_t r = 1, b = c.scale_w[l];
   while (e) {
-    if (e & 1) r = mulm(r, b, m);
-    b = mulm(b, b, m);
+    if (e & 1) r = red64((uint64_t)r * b, p, mu);
+    b = red64((uint64_t)b * b, p, mu);
     e >>= 1;
   }
   return r;
@@ -99,13 +100,22 @@ __device__ __forceinline__ uint32_t scale_factor(const DevCtx& c, uint32_t l, ui
 // mod q_l.  Q m = (floor(Q/t) t + (Q mod t)) m, so it is floor(Q/t) m + fix with
 // fix = floor(((Q mod t) m + floor((t+1)/2)) / t) < t; the quotient comes from the
 // Barrett constant of t and one correction step.
-__device__ __forceinline__ uint32_t scaled_msg(const DevCtx& c, uint32_t l, uint32_t m) {
-  const uint64_t num = (uint64_t)c.rt * m + (c.t + 1) / 2;
-  uint64_t fix = __umul64hi(num, c.mt.mu);
-  if (num - fix * c.t >= c.t) fix++;
-  const ModP& mq = c.mq[l];
-  return addm(mulm(c.delta[l], m, mq), red64(fix, mq.p, mq.mu), mq.p);
-}
+// (The context is read by value: a reference into the kernel-parameter arrays with a
+// runtime index would make the compiler copy the whole parameter block to local
+// memory.)
+struct ScaledMsg {
+  uint32_t rt, t, half, dl, p;
+  uint64_t tmu, pmu;
+  __device__ __forceinline__ ScaledMsg(const DevCtx& c, uint32_t l)
+      : rt(c.rt), t(c.t), half((c.t + 1) / 2), dl(c.delta[l]), p(c.mq[l].p), tmu(c.mt.mu),
+        pmu(c.mq[l].mu) {}
+  __device__ __forceinline__ uint32_t operator()(uint32_t m) const {
+    const uint64_t num = (uint64_t)rt * m + half;
+    uint64_t fix = __umul64hi(num, tmu);
+    if (num - fix * t >= t) fix++;
+    return addm(red64((uint64_t)dl * m, p, pmu), red64(fix, p, pmu), p);
+  }
+};
 
 // shared-memory index with one pad word per 32 (bank-conflict-free NTT passes)
 __device__ __forceinline__ uint32_t padi(uint32_t i) { return i + (i >> 5); }

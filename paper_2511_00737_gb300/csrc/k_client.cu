@@ -26,7 +26,7 @@ __device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t 
 // One CTA per plaintext (g, i).  The query slots are packed (pack_query_slots), the
 // inverse NTT mod t gives the plaintext coefficients, and for each limb the centred
 // lift feeds the forward NTT, whose output is staged in shared memory and stored
-// with 16-byte writes.
+// with 16-byte writes.  (The scaling operation, when on, is a separate pass.)
 template <int LOGN, int V>
 __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
     k_encode_plain(DevCtx c, const int8_t* __restrict__ H, int B, uint32_t* __restrict__ pt) {
@@ -51,22 +51,32 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
     };
     ntt_fwd_io<LOGN, decltype(lift), SmemSt, V>(wb, m, lift, SmemSt{wb});
     uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
-    if (c.scale_g == 0) {
-      for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
-        dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
-                            wb[padi(4 * k + 3)]);
-    } else {
-      // scaling operation folded into the plaintext: the accumulator scaled after
-      // every g products equals, mod q_l, the sum of the products with plaintext i
-      // multiplied by w^(floor(P/g) - floor(i/g))
-      const uint32_t w = scale_factor(c, l, c.P / c.scale_g - i / c.scale_g);
-      const uint32_t wsh = (uint32_t)(((uint64_t)w << 32) / p);
-      auto sc = [=](uint32_t v) { return csub(mulshoup(v, w, wsh, p), p); };
-      for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
-        dst[k] = make_uint4(sc(wb[padi(4 * k)]), sc(wb[padi(4 * k + 1)]),
-                            sc(wb[padi(4 * k + 2)]), sc(wb[padi(4 * k + 3)]));
-    }
+    for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
+      dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
+                          wb[padi(4 * k + 3)]);
     __syncthreads();
+  }
+}
+
+// Scaling operation folded into the plaintexts (only when it is on): the accumulator
+// scaled after every g products equals, mod q_l, the sum of the products with
+// plaintext i multiplied by w^(floor(P/g) - floor(i/g)).  One CTA per plaintext.
+__global__ void __launch_bounds__(256) k_scale_plain(DevCtx c, uint32_t* __restrict__ pt) {
+  const uint32_t gi = blockIdx.x;
+  const uint32_t i = gi % c.P;
+  for (uint32_t l = 0; l < c.L; l++) {
+    const uint32_t p = c.mq[l].p;
+    const uint32_t w = scale_factor(c, l, c.P / c.scale_g - i / c.scale_g);
+    const uint32_t wsh = (uint32_t)(((uint64_t)w << 32) / p);
+    uint4* q = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * c.n);
+    for (uint32_t k = threadIdx.x; k < c.n / 4; k += blockDim.x) {
+      uint4 v = q[k];
+      v.x = csub(mulshoup(v.x, w, wsh, p), p);
+      v.y = csub(mulshoup(v.y, w, wsh, p), p);
+      v.z = csub(mulshoup(v.z, w, wsh, p), p);
+      v.w = csub(mulshoup(v.w, w, wsh, p), p);
+      q[k] = v;
+    }
   }
 }
 
@@ -384,6 +394,7 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
     if (e != cudaSuccess) return e;
     kern<<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
   });
+  if (c.scale_g) k_scale_plain<<<G * c.P, 256, 0, st>>>(c, pt);
   return cudaGetLastError();
 }
 

@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
   ntt_inv_smem(mb, c.logn, c.mt);  // m in [0, t)
   // the scaled message round(q m / t) is formed per coefficient (it is not linear in
   // m), then transformed with a and e
-  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x)
-    mb[padi(x)] = scaled_msg(c, l, mb[padi(x)]);
+  const ScaledMsg scaled(c, l);
+  for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) mb[padi(x)] = scaled(mb[padi(x)]);
   __syncthreads();
   ntt_fwd_smem(mb, c.logn, m);
   ntt_fwd_smem(ab, c.logn, m);

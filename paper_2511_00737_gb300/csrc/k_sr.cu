@@ -55,10 +55,10 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 2)
   for (uint32_t l = 0; l < c.L; l++) {
     const ModP m = c.mq[l];
     const uint32_t p = m.p;
+    const ScaledMsg sm_l(c, l);
     auto dm_e = [=](uint32_t k) -> uint32_t {
       const int32_t e = eb[k];
-      return addm(scaled_msg(c, l, mb[padi(k)]), e < 0 ? (uint32_t)((int32_t)p + e) : (uint32_t)e,
-                  p);
+      return addm(sm_l(mb[padi(k)]), e < 0 ? (uint32_t)((int32_t)p + e) : (uint32_t)e, p);
     };
     ntt_fwd_io<LOGN, decltype(dm_e), SmemSt, V>(wb, m, dm_e, SmemSt{vb});
     fill_uniform(c, seed, 6, gi, l, wb);
