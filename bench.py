@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--workload", default="face1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-perquery", action="store_true")
+    ap.add_argument("--clientrt-table", action="store_true",
+                    help="only print the client-runtime table at the paper's parameters")
     ap.add_argument("--no-sr", action="store_true",
                     help="skip the client-runtime comparison with the server-side variant")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -500,6 +502,61 @@ def client_runtime(w, dev, B, reps=5):
             "same_scores": same}
 
 
+def clientrt_table(dev, reps=10):
+    """Table t:clientrt's four points at the paper's own parameters (Face: k = 2, the
+    SIMD layout k_in = k, r = 1, one batch of N/2 queries; q at the 128-bit bound
+    with 27-bit primes: 2 at N = 2048, 4 at N = 4096): client runtime of the
+    client-side path (EncPt + HE compute) and of the server-side variant
+    (encryption + decryption) on this GPU, and both message sizes."""
+    import torch
+    from paper_2511_00737_gb300 import ephdc as E
+    from paper_2511_00737_gb300 import workload as WL
+    rows = []
+    for N, D in [(2048, 1024), (2048, 2048), (4096, 1024), (4096, 2048)]:
+        L, F, seed = (2 if N == 2048 else 4), 608, 2511
+        cap = N // 2
+        ctx = E.Context(N, L, 2, 2, 1, D, F, 8, WL.default_shift(F, 8), cap, prime_bits=27)
+        sk, gk = ctx.keygen(seed)
+        cls = torch.from_numpy(WL.classes(seed, 2, D)).to(dev)
+        model = ctx.encrypt_model(cls, sk, seed)
+        Wt = torch.from_numpy(WL.projection(seed, D, F)).to(dev)
+        H = ctx.hdc_encode(torch.from_numpy(WL.features(seed, cap, F)).to(dev), Wt)
+        pt = ctx.encode_plain(H)
+        ctq = ctx.encrypt_queries(H, sk, seed)
+        mm = ctx.encode_model_plain(cls)
+        out, out_sr = ctx.out_ct(cap), ctx.out_ct(cap)
+        scores = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        encpt = timed(lambda: E.bfv_encode_plain(ctx.ctx, H, cap, pt))
+        he = timed(lambda: E.bfv_ptct_similarity(ctx.ctx, pt, cap, model, gk, out))
+        enc = timed(lambda: E.bfv_encrypt_queries(ctx.ctx, H, cap, sk, seed, ctq))
+        E.bfv_ctpt_similarity(ctx.ctx, ctq, cap, mm, gk, out_sr)
+        dec = timed(lambda: E.bfv_decrypt_scores(ctx.ctx, sk, out_sr, cap, scores))
+        same = bool(torch.equal(ctx.decrypt_scores(sk, out, cap), ctx.decrypt_scores(sk, out_sr, cap)))
+        rows.append({"N": N, "D": D, "L": L, "log2_q": round(sum(math.log2(q) for q in ctx.q), 1),
+                     "batch": cap,
+                     "client_side_ms": encpt + he, "encpt_ms": encpt, "he_compute_ms": he,
+                     "client_side_message_bytes": int(E.lib().ephdc_out_ct_bytes(ctx.ctx, cap)),
+                     "server_side_ms": enc + dec, "encrypt_ms": enc, "decrypt_ms": dec,
+                     "server_side_message_bytes": int(E.lib().ephdc_query_ct_bytes(ctx.ctx, cap)),
+                     "client_speedup": (enc + dec) / (encpt + he), "same_scores": same})
+        ctx.device_status()
+        ctx.close()
+    return rows
+
+
 def per_query_form(w, dev, queries=32):
     import torch
     from paper_2511_00737_gb300 import ephdc as E
@@ -650,6 +707,13 @@ def main():
         w.B = args.batch
         w.clients = []
     B = w.B
+    if args.clientrt_table:
+        import torch
+        rows = clientrt_table(torch.device("cuda"))
+        print(json.dumps({"table": "client runtime, client-side vs server-side HE (Table "
+                                   "t:clientrt shape), device ms per batch", "rows": rows}),
+              flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, w, B if B else 1024)
     elif args.workload == "serve" and not args.batch:

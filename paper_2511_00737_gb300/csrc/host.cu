@@ -1,8 +1,11 @@
 // Host side of the EP-HDC CUDA library: parameter derivation, device tables,
 // context and scratch management, and the C-ABI entry points declared in
-// include/ephdc.h.  Every step of the inference path runs in the kernels of
-// k_hdc.cu, k_client.cu and k_server.cu; this file only validates arguments,
-// derives constants and enqueues launches.
+// include/ephdc.h.  Every step of the inference path runs in the kernels of the
+// k_*.cu files; this file only validates arguments, derives constants and enqueues
+// launches.  Each stage is an NVTX range (header-only NVTX: free unless a profiler
+// is attached) and, when profiling is on, a pair of CUDA events.
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -138,12 +141,17 @@ static cudaEvent_t take_event(ephdc_ctx* c) {
 }
 
 // RAII bracket: records an event pair around one stage on the call's stream
+const char* const kStageNames[EPHDC_NSTAGES] = {"ephdc.hdc_encode", "ephdc.encode_plain",
+                                                "ephdc.mac", "ephdc.rotate", "ephdc.export",
+                                                "ephdc.encrypt_queries"};
+
 struct StageTimer {
   ephdc_ctx* c;
   cudaStream_t st;
   ephdc_ctx::Rec r{};
   StageTimer(ephdc_ctx* c_, int stage, cudaStream_t st_, uint64_t nlaunch) : c(c_), st(st_) {
     c->launches += nlaunch;
+    nvtxRangePushA(kStageNames[stage]);
     if (!c->prof) return;
     r.stage = stage;
     r.a = take_event(c);
@@ -151,6 +159,7 @@ struct StageTimer {
     cudaEventRecord(r.a, st);
   }
   ~StageTimer() {
+    nvtxRangePop();
     if (!c->prof) return;
     cudaEventRecord(r.b, st);
     c->recs.push_back(r);

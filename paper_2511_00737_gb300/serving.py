@@ -16,6 +16,12 @@ Requests (one client's batch of feature rows each) arrive over time.  The loop
 
 Each request's result is the range of packed queries it owns in its step's score
 ciphertexts; decrypting them gives the same scores as running the request alone.
+
+A request can be cancelled at any time: while it waits it is dropped (and its
+memory returned); once launched its step runs to completion, the request's rows are
+discarded and its memory is returned with the step, so nothing in flight on the
+device is interrupted.  The slots are injectable (`slot_factory`), so the admission,
+packing, cancellation and bookkeeping logic runs on the host with fake slots.
 """
 import collections
 import math
@@ -30,7 +36,7 @@ from . import ephdc as E
 
 class Request:
     __slots__ = ("rid", "arrival", "X", "B", "admitted", "launched", "done", "step",
-                 "rows", "nbytes")
+                 "rows", "nbytes", "cancelled")
 
     def __init__(self, rid, arrival, X):
         self.rid, self.arrival, self.X = rid, arrival, X
@@ -39,6 +45,7 @@ class Request:
         self.step = None
         self.rows = None
         self.nbytes = 0
+        self.cancelled = False
 
 
 class Step:
@@ -63,15 +70,27 @@ class Slot:
             self.pipe.graph(G) if self.pipe.use_graphs else None
         torch.cuda.synchronize()
 
+    def submit(self, Xs):
+        """Launches one packed step on this slot's stream; returns (pinned host copy of
+        the score ciphertexts, completion event, PackedBatch)."""
+        with torch.cuda.stream(self.stream):
+            out, pb = self.pipe.launch(Xs, self.stream)
+            host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
+            host.copy_(out, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.stream)
+        return host, ev, pb
+
 
 class Server:
     def __init__(self, w, Wt, model, gk, slots=2, max_groups=8, budget_bytes=None,
-                 use_graphs=True, keep_outputs=False):
+                 use_graphs=True, keep_outputs=False, slot_factory=None):
         self.w = w
         self.cap = 2 * ((w.n // (2 * w.r)) // w.k_in)
         self.ct_bytes = 2 * w.L * w.n * 4
         self.Kp = w.k // w.k_in
-        self.slots = [Slot(w, Wt, model, gk, max_groups, use_graphs) for _ in range(slots)]
+        make = slot_factory or (lambda i: Slot(w, Wt, model, gk, max_groups, use_graphs))
+        self.slots = [make(i) for i in range(slots)]
         self.max_queries = max_groups * self.cap
         if budget_bytes is None:
             free, _ = torch.cuda.mem_get_info()
@@ -84,6 +103,7 @@ class Server:
         self.steps = []
         self.completed = []
         self.rejected = []
+        self.cancelled = []
 
     def request_bytes(self, B):
         # the request's features on the device plus its share of score ciphertexts
@@ -118,12 +138,7 @@ class Server:
             total += r.B
         if not take:
             return False
-        with torch.cuda.stream(slot.stream):
-            out, pb = slot.pipe.launch([r.X for r in take], slot.stream)
-            host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
-            host.copy_(out, non_blocking=True)
-            ev = torch.cuda.Event()
-            ev.record(slot.stream)
+        host, ev, pb = slot.submit([r.X for r in take])
         st = Step(len(self.steps), take, pb, host, ev, slot)
         for i, r in enumerate(take):
             r.launched, r.step, r.rows = now, st.sid, pb.rows(i)
@@ -141,7 +156,7 @@ class Server:
                 for r in st.reqs:
                     r.done = t
                     self.used -= r.nbytes
-                    self.completed.append(r)
+                    (self.cancelled if r.cancelled else self.completed).append(r)
                 if not self.keep_outputs:
                     st.host_out = None
                 slot.busy = None
@@ -150,6 +165,30 @@ class Server:
             if slot.busy is None and self.queue:
                 self._launch(slot, now)
         return bool(self.queue or self.pending or any(s.busy for s in self.slots))
+
+    def cancel(self, rid, now):
+        """Cancels request rid.  Waiting requests leave at once (admitted ones return
+        their memory); a launched request's step finishes, its rows are discarded and
+        its memory comes back with the step.  Returns False if rid is unknown or
+        already finished."""
+        for dq, admitted in ((self.pending, False), (self.queue, True)):
+            for r in dq:
+                if r.rid == rid:
+                    dq.remove(r)
+                    r.cancelled, r.done = True, now
+                    if admitted:
+                        self.used -= r.nbytes
+                    self.cancelled.append(r)
+                    self._admit(now)
+                    return True
+        for slot in self.slots:
+            st = slot.busy
+            if st is not None:
+                for r in st.reqs:
+                    if r.rid == rid and not r.cancelled:
+                        r.cancelled = True
+                        return True
+        return False
 
     # ------------------------------------------------------------------ driver
     def run(self, arrivals, make_X, time_scale=1.0):
@@ -174,8 +213,9 @@ class Server:
         lat = np.array([r.done - r.arrival for r in self.completed]) if self.completed else \
             np.zeros(1)
         q = sum(r.B for r in self.completed)
-        return {"requests": len(self.completed) + len(self.rejected),
+        return {"requests": len(self.completed) + len(self.rejected) + len(self.cancelled),
                 "completed": len(self.completed), "rejected": len(self.rejected),
+                "cancelled": len(self.cancelled),
                 "queries": q, "queries_per_s": q / wall_s if wall_s > 0 else 0.0,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
