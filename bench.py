@@ -51,7 +51,7 @@ def parse():
                     help="force the multiply-accumulate schedule (profiling)")
     ap.add_argument("--pack", type=int, default=0,
                     help="consecutive batches packed into one step (one model stream); "
-                         "0 = as many as fit in 8 query groups")
+                         "0 = as many as fit in 16 query groups")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
     return ap.parse_args()
@@ -217,7 +217,7 @@ def run_ours(args, w, B):
     # encrypted model is streamed once for all of their groups
     groups_per_batch = -(-B // cap)
     batch = B
-    pack = 1 if multi else (args.pack if args.pack > 0 else max(1, 8 // groups_per_batch))
+    pack = 1 if multi else (args.pack if args.pack > 0 else max(1, 16 // groups_per_batch))
     B = batch * pack
     if multi:
         from paper_2511_00737_gb300 import autotune as AT
@@ -588,7 +588,8 @@ def per_query_form(w, dev, queries=32):
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
 # the same kernel and launch shape (dram__bytes_read.sum + dram__bytes_write.sum):
 # (workload, groups per launch, stage) -> bytes
-NCU_TRAFFIC = {("face1024", 8, "encode_plain"): 1332334592}
+NCU_TRAFFIC = {("face1024", 8, "encode_plain"): 1332334592,
+               ("face1024", 16, "encode_plain"): 2724109056}
 
 
 def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
