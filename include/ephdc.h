@@ -48,7 +48,7 @@ extern "C" {
 typedef enum {
   EPHDC_OK = 0,
   EPHDC_EINVAL = -1,       /* bad argument (size, pointer, alignment, parameter)   */
-  EPHDC_EUNSUPPORTED = -2, /* valid but not supported by this build               */
+  EPHDC_EUNSUPPORTED = -2, /* valid but not supported by this library             */
   EPHDC_ENOMEM = -3,       /* device allocation failed / batch above the reserve  */
   EPHDC_ECUDA = -4,        /* a CUDA call or kernel launch failed                 */
   EPHDC_ETIMEOUT = -5,     /* a bounded device wait gave up                       */

@@ -86,7 +86,7 @@ class Workload:
 
 
 def config(name, **over):
-    """Workloads of the paper's shape (the survey's C1..C5), with optional overrides."""
+    """Named workloads with the shapes of the paper's experiments, with optional overrides."""
     base = {
         # 16 queries, F=608, D=2048, 4-bit HVs, 2 classes, n=4096, 3 primes; packed
         # layout A with r=128 (7 rotations).  Small enough for the oracle in seconds.
