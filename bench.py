@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--pack", type=int, default=0,
                     help="consecutive batches packed into one step (one model stream); "
                          "0 = as many as fit in 16 query groups")
+    ap.add_argument("--dim", type=int, default=0,
+                    help="override the hypervector dimension D (profiling of smaller cases)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
     return ap.parse_args()
@@ -707,6 +709,8 @@ def main():
     if args.batch:
         w.B = args.batch
         w.clients = []
+    if args.dim:
+        w.D = args.dim
     B = w.B
     if args.clientrt_table:
         import torch
