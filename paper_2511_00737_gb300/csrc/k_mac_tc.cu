@@ -8,8 +8,11 @@
 // rows (u, g) of the digit matrix A' (4 GP x K) times columns (v, o) of B' (K x 4 OP).
 // Bytes are fp16 values, products are < 2^16, and a window of 256 plaintexts keeps
 // every fp32 partial sum below 2^24: exact.  After each window the TMEM accumulator
-// is read out, each S_uv is multiplied by 2^(8(u+v)) mod q_l and added to 64-bit
-// shared accumulators (reduced once at the end); the next window restarts the MMA.
+// is read out: the 4 digit rows (u, g) of a group sit in one warp (lanes u*8 + g mod
+// 8), so each thread weights its S_uv by 2^(8(u+v)) mod q_l and sums over v in
+// registers, two shuffles sum over u, and the owner lane adds the result into the
+// group's accumulators (reduced mod q_l every window; no atomics).  The next window
+// restarts the MMA.
 //
 // One CTA: limb l, KB consecutive coefficients, one block of GP groups, all outputs.
 // Per 16-plaintext chunk: cp.async stages the raw residues (rows of KB words) into a
@@ -79,6 +82,16 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* v) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* dst, const void* src, bool ok) {
   const uint32_t d = smem_u32(dst);
@@ -106,6 +119,12 @@ __device__ __forceinline__ uint32_t op_off(uint32_t r, uint32_t k) {
   return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
+// A row of digit u of group g (g < 32 MT): the 4 digits of a group in one warp's
+// 32 TMEM lanes, lane u * 8 + g mod 8, warp quarter (g / 8) mod 4, M tile g / 32
+__device__ __forceinline__ uint32_t arow(uint32_t u, uint32_t g) {
+  return (g >> 3) * 32 + u * 8 + (g & 7);
+}
+
 template <int MT, int OP, int KB>
 struct TcCfg {
   static constexpr int GP = 32 * MT;               // groups per CTA: A rows (u, g) = 128 MT
@@ -127,7 +146,7 @@ struct TcCfg {
   static constexpr uint32_t IDESC =
       (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   static constexpr size_t SMEM =
-      1024 + NB * OPS_BYTES + RING * RAW_WORDS * 4 + KB * GP * OP * 8 + 128;
+      1024 + NB * OPS_BYTES + RING * RAW_WORDS * 4 + KB * GP * OP * 4 + 128;
 };
 
 template <int MT, int OP, int KB>
@@ -141,7 +160,7 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* ops = sm;                                                // [NB][KB][A | B]
   uint32_t* raw = (uint32_t*)(sm + C::NB * C::OPS_BYTES);           // [RING][ROWS][RSTRIDE]
-  unsigned long long* accs = (unsigned long long*)(raw + C::RING * C::RAW_WORDS);  // [KB][OP][GP]
+  uint32_t* accs = raw + C::RING * C::RAW_WORDS;                   // [KB][OP][GP], mod q_l
   uint64_t* bars = (uint64_t*)(accs + KB * GP * OP);                // MMA done, per buffer
   uint32_t* tslot = (uint32_t*)(bars + 4);
   uint32_t* Wsh = tslot + 2;                                        // 2^(8e) mod q_l, e < 7
@@ -236,10 +255,9 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
 #pragma unroll
       for (int j = 0; j < KB; j++) {
         uint8_t* tile = ob + j * (C::A_BYTES + C::B_BYTES) + (isA ? 0 : C::A_BYTES);
-        const int stride = isA ? GP : OP;
 #pragma unroll
         for (int u = 0; u < 4; u++)
-          *reinterpret_cast<uint32_t*>(tile + op_off(u * stride + rr, ii)) =
+          *reinterpret_cast<uint32_t*>(tile + op_off(isA ? arow(u, rr) : u * OP + rr, ii)) =
               digit_pair(x[j], y[j], u);
       }
     }
@@ -249,7 +267,6 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
     uint32_t w = 1;
     for (int e = 0; e < 7; e++, w = mulm(w, 256u, m)) Wsh[e] = w;
   }
-  const uint32_t accs_s = smem_u32(accs);
 
   for (int s = 0; s < C::RING - 1; s++) {
     if (s < nch) load_raw(s, s);
@@ -294,38 +311,41 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
       if (tid == 0) ok = alive && mbar_wait(smem_u32(&bars[buf]), (ch / C::NB) & 1, status, 12);
       alive = __syncthreads_and(alive && ok);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      if (alive) {
-        const int q = warp & 3, h = warp >> 2;
+      if (alive && warp < 4 * MT) {
+        // warp (mt, q) reads TMEM lanes 32 q of M tile mt: groups (4 mt + q) * 8 + lane % 8,
+        // digit u = lane / 8; all N columns (v, o)
+        const int mt = warp >> 2, q = warp & 3;
+        const int u = lane >> 3, g = (mt * 4 + q) * 8 + (lane & 7);
 #pragma unroll 1
-        for (int j = 0; j < KB; j++)
+        for (int j = 0; j < KB; j++) {
 #pragma unroll 1
-          for (int mt = 0; mt < MT; mt++) {
-            const int r = mt * 128 + 32 * q + lane;
-            const int u = r / GP, g = r - u * GP;
-            const bool row_ok = g0 + g < G;
-#pragma unroll 1
-            for (int x = 0; x < N / 64; x++) {
-              uint32_t v[32];
-              const int col0 = h * (N / 2) + x * 32;
-              tc_ld32(tmem + ((uint32_t)(32 * q) << 16) + (j * MT + mt) * N + col0, v);
-              if (row_ok) {
+          for (int oh = 0; oh < OP; oh += 16) {  // 16 outputs at a time
+            uint64_t t[16];
 #pragma unroll
-                for (int e = 0; e < 32; e++) {
-                  const int col = col0 + e, vv = col / OP, o = col - vv * OP;
-                  if (o < O) {
-                    // S_uv < 2^24 and 2^(8(u+v)) mod q < 2^30: products < 2^54, at most
-                    // 16 per window and 63 windows (P < 16384) stay below 2^64
-                    const uint32_t sv = (uint32_t)__float2uint_rz(__uint_as_float(v[e]));
-                    const uint64_t add = (uint64_t)sv * Wsh[u + vv];
-                    asm volatile("red.shared.add.u64 [%0], %1;\n" ::"r"(
-                                     accs_s + 8u * (uint32_t)((j * OP + o) * GP + g)),
-                                 "l"(add)
-                                 : "memory");
-                  }
-                }
-              }
+            for (int e = 0; e < 16; e++) t[e] = 0;
+#pragma unroll
+            for (int vv = 0; vv < 4; vv++) {
+              uint32_t v[16];
+              tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (j * MT + mt) * N + vv * OP + oh, v);
+              const uint64_t w = Wsh[u + vv];
+              // S_uv < 2^24 and 2^(8(u+v)) mod q < 2^30: 16 products per output < 2^58
+#pragma unroll
+              for (int e = 0; e < 16; e++)
+                t[e] += (uint64_t)__float2uint_rz(__uint_as_float(v[e])) * w;
+            }
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+              t[e] += __shfl_xor_sync(0xffffffffu, t[e], 8);
+              t[e] += __shfl_xor_sync(0xffffffffu, t[e], 16);
+            }
+            if (u == 0 && g0 + g < G) {
+              uint32_t* a = accs + (size_t)j * OP * GP + g;
+#pragma unroll
+              for (int e = 0; e < 16; e++)
+                if (oh + e < O) a[(oh + e) * GP] = red64(t[e] + a[(oh + e) * GP], m.p, m.mu);
             }
           }
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncthreads();
@@ -336,8 +356,7 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
     const int j = idx % KB, rest = idx / KB;
     const int o = rest % OP, g = rest / OP;
     if (g0 + g < G && o < O)
-      out[(((size_t)(g0 + g) * O + o) * L + l) * n + k0 + j] =
-          red64(accs[(j * OP + o) * GP + g], m.p, m.mu);
+      out[(((size_t)(g0 + g) * O + o) * L + l) * n + k0 + j] = accs[(j * OP + o) * GP + g];
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
