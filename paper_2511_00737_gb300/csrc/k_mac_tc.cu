@@ -139,9 +139,9 @@ struct TcCfg {
   static constexpr int A_BYTES = 4 * GP * KC * 2;  // per coefficient
   static constexpr int B_BYTES = N * KC * 2;
   static constexpr int OPS_BYTES = KB * (A_BYTES + B_BYTES);  // one operand buffer
-  // operand buffers in flight (the MMAs of chunk c must finish before chunk c + NB
-  // reuses their buffer); deeper rings cost occupancy and measured slower
-  static constexpr int NB = 2;
+  // operand buffers in flight (the MMAs of chunk c, issued one iteration after its
+  // split, must finish before chunk c + NB reuses the buffer)
+  static constexpr int NB = 3;
   static constexpr int TCOLS = KB * MT * N;                   // TMEM columns
   static constexpr uint32_t IDESC =
       (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
   uint8_t* ops = sm;                                                // [NB][KB][A | B]
   uint32_t* raw = (uint32_t*)(sm + C::NB * C::OPS_BYTES);           // [RING][ROWS][RSTRIDE]
   uint32_t* accs = raw + C::RING * C::RAW_WORDS;                   // [KB][OP][GP], mod q_l
-  uint64_t* bars = (uint64_t*)(accs + KB * GP * OP);                // MMA done, per buffer
+  uint64_t* bars = (uint64_t*)(accs + KB * GP * OP);                // MMA done, per buffer (NB <= 4)
   uint32_t* tslot = (uint32_t*)(bars + 4);
   uint32_t* Wsh = tslot + 2;                                        // 2^(8e) mod q_l, e < 7
 
@@ -272,28 +272,58 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
     if (s < nch) load_raw(s, s);
     else asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
+  // window read-out: warp (mt, q) reads TMEM lanes 32 q of M tile mt, i.e. groups
+  // (4 mt + q) * 8 + lane % 8 with digit u = lane / 8, and all N columns (v, o)
+  auto readout = [&]() {
+    if (warp >= 4 * MT) return;
+    const int mt = warp >> 2, q = warp & 3;
+    const int u = lane >> 3, g = (mt * 4 + q) * 8 + (lane & 7);
+#pragma unroll 1
+    for (int j = 0; j < KB; j++) {
+#pragma unroll 1
+      for (int oh = 0; oh < OP; oh += 16) {  // 16 outputs at a time
+        uint64_t t[16];
+#pragma unroll
+        for (int e = 0; e < 16; e++) t[e] = 0;
+#pragma unroll
+        for (int vv = 0; vv < 4; vv++) {
+          uint32_t v[16];
+          tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (j * MT + mt) * N + vv * OP + oh, v);
+          const uint64_t w = Wsh[u + vv];
+          // S_uv < 2^24 and 2^(8(u+v)) mod q < 2^30: 16 products per output < 2^58
+#pragma unroll
+          for (int e = 0; e < 16; e++)
+            t[e] += (uint64_t)__float2uint_rz(__uint_as_float(v[e])) * w;
+        }
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+          t[e] += __shfl_xor_sync(0xffffffffu, t[e], 8);
+          t[e] += __shfl_xor_sync(0xffffffffu, t[e], 16);
+        }
+        if (u == 0 && g0 + g < G) {
+          uint32_t* a = accs + (size_t)j * OP * GP + g;
+#pragma unroll
+          for (int e = 0; e < 16; e++)
+            if (oh + e < O) a[(oh + e) * GP] = red64(t[e] + a[(oh + e) * GP], m.p, m.mu);
+        }
+      }
+    }
+  };
+
+  // One block barrier per chunk: at the top of iteration ch every thread's copies of
+  // chunk ch have landed and every operand tile of chunk ch - 1 is written, so thread
+  // 0 issues the MMAs of chunk ch - 1 while the block loads and splits chunk ch.  An
+  // operand buffer is reused NB chunks later, after each thread has seen the MMAs
+  // that read it complete (every chunk's completion is awaited in order, so the
+  // mbarrier parity is never more than one phase ahead).
   bool alive = true;
-  for (int ch = 0; ch < nch; ch++) {
-    const int buf = ch % C::NB;
+  for (int ch = 0; ch <= nch; ch++) {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(C::RING - 2) : "memory");
-    __syncthreads();
-    {
-      const int nx = ch + C::RING - 1;
-      if (nx < nch) load_raw(nx, nx % C::RING);
-      else asm volatile("cp.async.commit_group;\n" ::: "memory");
-    }
-    if (ch >= C::NB) {  // operand buffer `buf` was read by the MMAs of chunk ch - NB
-      bool ok = true;
-      if (tid == 0)
-        ok = mbar_wait(smem_u32(&bars[buf]), ((ch - C::NB) / C::NB) & 1, status, 11);
-      alive = __syncthreads_and(alive && ok);
-    }
-    if (alive) transform(ch % C::RING, buf);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0 && alive) {
+    alive = __syncthreads_and(alive);
+    const int pc = ch - 1;
+    if (pc >= 0 && tid == 0 && alive) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t ob = smem_u32(ops + buf * C::OPS_BYTES);
+      const uint32_t ob = smem_u32(ops + (pc % C::NB) * C::OPS_BYTES);
 #pragma unroll
       for (int j = 0; j < KB; j++) {
         const uint32_t a0 = ob + j * (C::A_BYTES + C::B_BYTES), b0 = a0 + C::A_BYTES;
@@ -301,55 +331,30 @@ __global__ void __launch_bounds__(256, 1) k_mac_tc(DevCtx c, const uint32_t* __r
 #pragma unroll
         for (int mt = 0; mt < MT; mt++)
           tc_mma<C::IDESC>(tmem + (j * MT + mt) * N, sdesc_noswz(a0 + mt * 4096, 128, 256), bd,
-                           (ch % C::WIN) != 0);
+                           (pc % C::WIN) != 0);
       }
-      tc_commit(smem_u32(&bars[buf]));
+      tc_commit(smem_u32(&bars[pc % C::NB]));
     }
-    if ((ch % C::WIN) == C::WIN - 1 || ch == nch - 1) {
-      // window complete: every S_uv of these 256 plaintexts is in TMEM
-      bool ok = true;
-      if (tid == 0) ok = alive && mbar_wait(smem_u32(&bars[buf]), (ch / C::NB) & 1, status, 12);
-      alive = __syncthreads_and(alive && ok);
+    if (pc >= 0 && ((pc % C::WIN) == C::WIN - 1 || pc == nch - 1)) {
+      // window complete: every S_uv of its plaintexts is in TMEM
+      const bool ok =
+          alive && mbar_wait(smem_u32(&bars[pc % C::NB]), (pc / C::NB) & 1, status, 12);
+      alive = __syncthreads_and(ok);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      if (alive && warp < 4 * MT) {
-        // warp (mt, q) reads TMEM lanes 32 q of M tile mt: groups (4 mt + q) * 8 + lane % 8,
-        // digit u = lane / 8; all N columns (v, o)
-        const int mt = warp >> 2, q = warp & 3;
-        const int u = lane >> 3, g = (mt * 4 + q) * 8 + (lane & 7);
-#pragma unroll 1
-        for (int j = 0; j < KB; j++) {
-#pragma unroll 1
-          for (int oh = 0; oh < OP; oh += 16) {  // 16 outputs at a time
-            uint64_t t[16];
-#pragma unroll
-            for (int e = 0; e < 16; e++) t[e] = 0;
-#pragma unroll
-            for (int vv = 0; vv < 4; vv++) {
-              uint32_t v[16];
-              tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (j * MT + mt) * N + vv * OP + oh, v);
-              const uint64_t w = Wsh[u + vv];
-              // S_uv < 2^24 and 2^(8(u+v)) mod q < 2^30: 16 products per output < 2^58
-#pragma unroll
-              for (int e = 0; e < 16; e++)
-                t[e] += (uint64_t)__float2uint_rz(__uint_as_float(v[e])) * w;
-            }
-#pragma unroll
-            for (int e = 0; e < 16; e++) {
-              t[e] += __shfl_xor_sync(0xffffffffu, t[e], 8);
-              t[e] += __shfl_xor_sync(0xffffffffu, t[e], 16);
-            }
-            if (u == 0 && g0 + g < G) {
-              uint32_t* a = accs + (size_t)j * OP * GP + g;
-#pragma unroll
-              for (int e = 0; e < 16; e++)
-                if (oh + e < O) a[(oh + e) * GP] = red64(t[e] + a[(oh + e) * GP], m.p, m.mu);
-            }
-          }
-        }
-      }
+      if (alive) readout();
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncthreads();
     }
+    if (ch == nch) break;
+    {  // raw stage of chunk ch - 1 is free: load chunk ch + RING - 1 into it
+      const int nx = ch + C::RING - 1;
+      if (nx < nch) load_raw(nx, nx % C::RING);
+      else asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    if (ch >= C::NB && alive &&
+        !mbar_wait(smem_u32(&bars[ch % C::NB]), ((ch - C::NB) / C::NB) & 1, status, 11))
+      alive = false;
+    if (alive) transform(ch % C::RING, ch % C::NB);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   }
   __syncthreads();
   for (int idx = tid; idx < KB * GP * OP; idx += blockDim.x) {
