@@ -137,7 +137,9 @@ ephdc_status hdc_encode(ephdc_ctx* ctx, const int8_t* X_dev, const int8_t* Wt_de
 
 /* Batch-encode query hypervectors into BFV plaintexts (EncPt): slot packing per
  * (k_in, r), inverse NTT mod t (slot -> coefficient), centred lift and forward
- * NTT per RNS limb.  H_dev: int8 [B][D].  pt_dev: ephdc_plain_bytes(B). */
+ * NTT per RNS limb.  H_dev: int8 [B][D] (with r = 8 or 16 at k_in = 1, or r = 4 at
+ * k_in = 2, and D a multiple of r, query rows are read by vector loads; other layouts
+ * byte by byte, same result).  pt_dev: ephdc_plain_bytes(B). */
 ephdc_status bfv_encode_plain(ephdc_ctx* ctx, const int8_t* H_dev, int32_t B, uint32_t* pt_dev,
                               void* stream);
 

@@ -45,7 +45,7 @@ struct DevCtx {
   const uint32_t* slot2pos;  // slot index -> device NTT position
   const uint32_t* galois;    // galois[j] = 3^(W*2^j) mod 2n, j < logr
   const uint32_t* scatter;   // [(qidx * r + ch) * k_in + jin] -> device position
-  uint32_t pack_rows;        // r (8 or 16) when query rows pack by vector loads, else 0
+  uint32_t pack_rows;        // r when query rows pack by vector loads, else 0
   // context scratch used by kernels: fp16 copies of the HDC operands, status word
   uint16_t* xh;              // [max_batch][F] fp16 features
   uint16_t* wh;              // [D][F] fp16 projection
@@ -535,40 +535,44 @@ __device__ __forceinline__ void fill_gauss(const DevCtx& c, uint64_t seed, uint3
 // jin*cap_row + qq) for every jin < k_in.  Each value goes to its k_in device
 // positions through the context's scatter table.  No barrier.
 //
-// Rows path (c.pack_rows = r in {8, 16}: k_in = 1, D a multiple of r, H aligned to
-// r bytes): a thread takes whole query rows, the row's r bytes in one vector load and
-// its r table entries in 16-byte loads, and issues the loads of 32 / r rows before
-// the first store, so a CTA waits for one memory round trip instead of one per row.
+// Rows path (c.pack_rows = r, with (r, k_in) one of (8, 1), (16, 1), (4, 2): D a
+// multiple of r, H aligned to r bytes): a thread takes whole query rows, the row's r
+// bytes in one vector load and its r k_in table entries in 16-byte loads, and issues
+// the loads of 32 / (r k_in) rows before the first store, so a CTA waits for one
+// memory round trip instead of one per row.
 // Generic path: threads walk the cap x r block of H byte by byte (consecutive
 // threads read consecutive bytes of a query row).
 template <int R> struct PackRow;
+template <> struct PackRow<4> { using T = uint32_t; };
 template <> struct PackRow<8> { using T = uint2; };
 template <> struct PackRow<16> { using T = uint4; };
 
+__device__ __forceinline__ uint32_t row_word(uint32_t v, int) { return v; }
 __device__ __forceinline__ uint32_t row_word(const uint2& v, int w) { return w ? v.y : v.x; }
 __device__ __forceinline__ uint32_t row_word(const uint4& v, int w) {
   return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
 }
 
-template <int R>
+template <int R, int KIN>
 __device__ __forceinline__ void pack_query_rows(const DevCtx& c, const int8_t* __restrict__ H,
                                                 uint32_t qlim, uint32_t g, uint32_t i,
                                                 uint32_t* mb) {
   using Row = typename PackRow<R>::T;
-  constexpr int QPT = 32 / R;  // rows in flight per thread
+  constexpr int E = R * KIN;     // table entries per row (a multiple of 4)
+  constexpr int QPT = 32 / E;    // rows in flight per thread
   const uint32_t D = c.D;
   const int8_t* Hg = H + (size_t)g * c.cap * D + (size_t)i * R;
   for (uint32_t q0 = threadIdx.x; q0 < qlim; q0 += QPT * blockDim.x) {
     Row hv[QPT];
-    uint4 sc[QPT][R / 4];
+    uint4 sc[QPT][E / 4];
 #pragma unroll
     for (int u = 0; u < QPT; u++) {
       const uint32_t q = q0 + u * blockDim.x;
       if (q < qlim) {
         hv[u] = __ldg(reinterpret_cast<const Row*>(Hg + (size_t)q * D));
-        const uint4* st = reinterpret_cast<const uint4*>(c.scatter + (size_t)q * R);
+        const uint4* st = reinterpret_cast<const uint4*>(c.scatter + (size_t)q * E);
 #pragma unroll
-        for (int v = 0; v < R / 4; v++) sc[u][v] = __ldg(st + v);
+        for (int v = 0; v < E / 4; v++) sc[u][v] = __ldg(st + v);
       }
     }
 #pragma unroll
@@ -577,8 +581,12 @@ __device__ __forceinline__ void pack_query_rows(const DevCtx& c, const int8_t* _
 #pragma unroll
       for (int e = 0; e < R; e++) {
         const int h = (int)(int8_t)(row_word(hv[u], e >> 2) >> (8 * (e & 3)));
-        const uint32_t pos = row_word(sc[u][e >> 2], e & 3);
-        mb[padi(pos)] = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
+        const uint32_t v = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
+#pragma unroll
+        for (int j = 0; j < KIN; j++) {
+          const int x = e * KIN + j;
+          mb[padi(row_word(sc[u][x >> 2], x & 3))] = v;
+        }
       }
     }
   }
@@ -589,8 +597,9 @@ __device__ __forceinline__ void pack_query_slots(const DevCtx& c, const int8_t* 
   const uint32_t qlim = min((uint32_t)c.cap, (uint32_t)(B - (int)(g * c.cap)));
   const uint32_t rows = c.pack_rows;
   if (rows && ((uintptr_t)H & (rows - 1)) == 0) {
-    if (rows == 8) return pack_query_rows<8>(c, H, qlim, g, i, mb);
-    if (rows == 16) return pack_query_rows<16>(c, H, qlim, g, i, mb);
+    if (rows == 8) return pack_query_rows<8, 1>(c, H, qlim, g, i, mb);
+    if (rows == 16) return pack_query_rows<16, 1>(c, H, qlim, g, i, mb);
+    if (rows == 4) return pack_query_rows<4, 2>(c, H, qlim, g, i, mb);
   }
   const uint32_t d0 = i * c.r;
   const uint32_t r = c.r, logr = c.logr, kin = c.k_in, D = c.D;

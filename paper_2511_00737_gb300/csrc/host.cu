@@ -350,7 +350,8 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   d.pos2slot = d.slot2pos + n;
   d.scatter = d.slot2pos + 2 * n;
   // whole query rows of r bytes fit one vector load when every row chunk is full
-  d.pack_rows = (d.k_in == 1 && (d.r == 8 || d.r == 16) && d.D % d.r == 0) ? d.r : 0;
+  d.pack_rows = (((d.k_in == 1 && (d.r == 8 || d.r == 16)) || (d.k_in == 2 && d.r == 4)) &&
+                 d.D % d.r == 0) ? d.r : 0;
   d.galois = (const uint32_t*)((uint8_t*)c->tables + align256(tw_bytes) + align256(map_bytes));
   cudaError_t ce = cudaMemcpy(c->tables, host.data(), total, cudaMemcpyHostToDevice);
   if (ce != cudaSuccess) {

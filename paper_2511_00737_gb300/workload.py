@@ -93,6 +93,9 @@ def config(name, **over):
         "small": dict(n=4096, L=3, k=2, k_in=2, r=128, D=2048, F=608, bits=4, B=16),
         # 1024 queries, F=608, D=10000, 8-bit HVs, 2 classes, n=8192, 4 primes
         "face1024": dict(n=8192, L=4, k=2, k_in=1, r=8, D=10000, F=608, bits=8, B=1024),
+        # the same batch in the paper's packed layout A: both classes in one ciphertext
+        # (k_in = k = 2), r = 4 (P = 2500 plaintexts, 2 rotations)
+        "face1024_a": dict(n=8192, L=4, k=2, k_in=2, r=4, D=10000, F=608, bits=8, B=1024),
         # the same batch in the per-query form: one query at a time, D folded over
         # n/(2 k_in) chunks (HE-HDC's dense shape, log2 r rotations per query)
         "face1024_perquery": dict(n=8192, L=4, k=2, k_in=2, r=2048, D=10000, F=608, bits=8,

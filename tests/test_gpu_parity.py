@@ -173,6 +173,10 @@ LAYOUTS = [
     (2048, 2, 7, 7, 2, 33, 64, 8, 300),     # 7 packed classes, cap_row = floor(512/7)
     (4096, 3, 2, 1, 16, 300, 48, 6, 1000),  # 4 rotations, G = 4 with a partial tail
     (1024, 4, 5, 5, 8, 100, 32, 8, 17),     # 3 rotations, cap_row = 12, B < cap
+    # D a multiple of r: whole query rows packed by vector loads, partial last group
+    (2048, 2, 3, 1, 8, 96, 32, 8, 300),     # 8-byte rows, G = 2 (256 + 44)
+    (4096, 3, 2, 1, 16, 320, 48, 8, 200),   # 16-byte rows, B < cap
+    (2048, 2, 2, 2, 4, 100, 32, 8, 300),    # layout A rows: 4 bytes, 2 positions each
 ]
 
 
@@ -273,4 +277,23 @@ def test_every_ntt_plan_gives_the_same_plaintexts(n, L, r):
             assert np.array_equal(got, _lifted(m.reshape(G * o.P, n), o.q))
         else:
             assert torch.equal(pt, ref), v
+    ctx.close()
+
+
+@pytest.mark.parametrize("r,k_in,D,B", [(8, 1, 96, 300), (16, 1, 96, 300), (4, 2, 100, 300),
+                                         (8, 1, 96, 1), (4, 2, 100, 257)])
+def test_query_row_pack_matches_oracle(r, k_in, D, B):
+    """Shapes whose query rows are packed by vector loads (D a multiple of r), with full,
+    partial and single-query groups: plaintexts equal to the oracle's."""
+    w = WL.Workload(name="t", n=2048, L=2, k=2, k_in=k_in, r=r, D=D, F=32, bits=8, B=B,
+                    seed=77 + r + B)
+    ctx = E.Context.for_workload(w)
+    X = WL.features(w.seed, w.B, w.F)
+    Wt = WL.projection(w.seed, w.D, w.F)
+    pt = ctx.encode_plain(ctx.hdc_encode(_dev(X), _dev(Wt)))
+    o = O.Oracle(w.n, w.L, w.k, w.k_in, w.r, w.D)
+    m = o.encode_plain(O.hdc_encode(X, Wt, w.shift, w.bits))
+    G = o.groups(w.B)
+    got = ctx.plain_to_host_coeff(pt, G * o.P)
+    assert np.array_equal(got, _lifted(m.reshape(G * o.P, w.n), o.q))
     ctx.close()
