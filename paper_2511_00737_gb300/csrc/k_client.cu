@@ -36,8 +36,13 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
   uint32_t* wb = sm + padded_words(N);
   const uint32_t gi = blockIdx.x;
   const uint32_t g = gi / c.P, i = gi - g * c.P;
-  for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) mb[padi(j)] = 0;
-  __syncthreads();
+  // with cap r k_in = n, a full group and a full D-chunk write every slot exactly once
+  const bool every_slot = c.cap * c.r * c.k_in == N && (g + 1) * c.cap <= (uint32_t)B &&
+                          (i + 1) * c.r <= c.D;
+  if (!every_slot) {
+    for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) mb[padi(j)] = 0;
+    __syncthreads();
+  }
   pack_query_slots(c, H, B, g, i, mb);
   __syncthreads();
   ntt_inv_t<LOGN, V>(mb, c.mt);  // slots -> coefficients in [0, t)
