@@ -280,10 +280,16 @@ __global__ void k_mac_reduce(DevCtx c, const uint32_t* __restrict__ partial, int
 }
 
 // ------------------------------------------------------------------ rotations
+// resident CTAs of at most 256 threads the key-switch kernels are compiled for: three
+// (80 registers) at n = 8192, two (128 registers) at n = 16384, where the transform
+// passes need more; smaller rings launch fewer threads and need no bound
+constexpr int ks_min_blocks(int logn) { return logn == 13 ? 3 : logn >= 14 ? 2 : 1; }
+
 // digits[ct][i][:] = INTT_{q_i}(tau_g(c1 limb i)): the RNS digits of the rotated c1
 // as integer polynomials with coefficients in [0, q_i).
 template <int LOGN>
-__global__ void __launch_bounds__(512) k_ks_digits(DevCtx c, const uint32_t* __restrict__ acc,
+__global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
+    k_ks_digits(DevCtx c, const uint32_t* __restrict__ acc,
                                                    uint32_t* __restrict__ digits, uint32_t gal) {
   constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
@@ -295,41 +301,35 @@ __global__ void __launch_bounds__(512) k_ks_digits(DevCtx c, const uint32_t* __r
 }
 
 // Key switch and add, one thread-block cluster of L CTAs per (ciphertext, target limb
-// l); cluster rank i owns RNS digit i:
-//   P0_i = NTT_l(d_i) * k0[i][l],  P1_i = NTT_l(d_i) * k1[i][l]   (in its shared memory)
-// then rank i sums its 1/L slice of the coefficients over the whole cluster through
-// distributed shared memory:
-//   out[ct][0][l] = acc0 + tau(acc0) + sum_i P0_i,   out[ct][1][l] = acc1 + sum_i P1_i.
-// For i = l the digit's transform is tau(acc1 limb l) itself and is read directly.
+// l); cluster rank i owns RNS digit i and holds X_i = NTT_l(d_i) in its shared memory
+// (for i = l the digit's transform is tau(acc1 limb l) itself, read directly).  Rank i
+// then produces its 1/L slice of the coefficients, reading every rank's X_r through
+// distributed shared memory and multiplying by that rank's key parts:
+//   out[ct][0][l] = acc0 + tau(acc0) + sum_r X_r * k0[r][l],
+//   out[ct][1][l] = acc1 + sum_r X_r * k1[r][l].
+// One transform buffer per CTA (the products are formed in the reduction).
 // gkj: [L digits][L limbs][4][n] = (k0, k0 Shoup, k1, k1 Shoup), NTT domain.
 template <int LOGN>
-__global__ void __launch_bounds__(512) k_ks_cluster(DevCtx c, const uint32_t* __restrict__ acc,
+__global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
+    k_ks_cluster(DevCtx c, const uint32_t* __restrict__ acc,
                                                     const uint32_t* __restrict__ digits,
                                                     const uint32_t* __restrict__ gkj,
                                                     uint32_t* __restrict__ out, uint32_t gal) {
   constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
-  uint32_t* p0 = sm;                    // padded, also the transform buffer
-  uint32_t* p1 = sm + padded_words(N);  // padded
+  uint32_t* x = sm;  // padded transform buffer
   cg::cluster_group cluster = cg::this_cluster();
   const uint32_t i = blockIdx.x, l = blockIdx.y, ct = blockIdx.z;
   const ModP m = c.mq[l];
   const uint32_t p = m.p;
-  const uint32_t* k = gkj + ((size_t)i * c.L + l) * 4 * N;
   const uint32_t* c1 = acc + ((size_t)(ct * 2 + 1) * c.L + l) * N;
   if (i == l) {
     for (uint32_t j = threadIdx.x; j < N; j += blockDim.x)
-      p0[padi(j)] = __ldg(&c1[galois_pos(j, gal, LOGN)]);
+      x[padi(j)] = __ldg(&c1[galois_pos(j, gal, LOGN)]);
   } else {
     const uint32_t* dg = digits + ((size_t)ct * c.L + i) * N;
-    ntt_fwd_io<LOGN>(p0, m, [=](uint32_t kk) { return csub(__ldg(&dg[kk]), p); },  // d < 2 q_l
-                     SmemSt{p0});
-  }
-  __syncthreads();
-  for (uint32_t j = threadIdx.x; j < N; j += blockDim.x) {
-    const uint32_t x = p0[padi(j)];
-    p0[padi(j)] = mulshoup(x, __ldg(&k[j]), __ldg(&k[N + j]), p);
-    p1[padi(j)] = mulshoup(x, __ldg(&k[2 * N + j]), __ldg(&k[3 * N + j]), p);
+    ntt_fwd_io<LOGN>(x, m, [=](uint32_t kk) { return csub(__ldg(&dg[kk]), p); },  // d < 2 q_l
+                     SmemSt{x});
   }
   cluster.sync();
   const uint32_t L = c.L;
@@ -342,10 +342,10 @@ __global__ void __launch_bounds__(512) k_ks_cluster(DevCtx c, const uint32_t* __
     uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[galois_pos(j, gal, LOGN)]);
     uint64_t s1 = __ldg(&c1[j]);
     for (uint32_t r = 0; r < L; r++) {
-      const uint32_t* q0 = cluster.map_shared_rank(p0, r);
-      const uint32_t* q1 = cluster.map_shared_rank(p1, r);
-      s0 += q0[padi(j)];
-      s1 += q1[padi(j)];
+      const uint32_t v = cluster.map_shared_rank(x, r)[padi(j)];
+      const uint32_t* k = gkj + ((size_t)r * L + l) * 4 * N + j;
+      s0 += mulshoup(v, __ldg(k), __ldg(k + N), p);  // each term < 2p
+      s1 += mulshoup(v, __ldg(k + 2 * N), __ldg(k + 3 * N), p);
     }
     o0[j] = red64(s0, p, m.mu);
     o1[j] = red64(s1, p, m.mu);
@@ -472,7 +472,9 @@ cudaError_t launch_mac_reduce(const DevCtx& c, const uint32_t* partial, int spli
 cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
                               int count, const uint32_t* gk, cudaStream_t st) {
   const size_t smem1 = padded_words(c.n) * sizeof(uint32_t);
-  const size_t smem2 = 2 * padded_words(c.n) * sizeof(uint32_t);
+  const size_t smem2 = padded_words(c.n) * sizeof(uint32_t);
+  // at most 256 threads per CTA (see ks_min_blocks)
+  const unsigned ks_threads = ntt_threads(c) < 256 ? ntt_threads(c) : 256;
   uint32_t* cur = acc;
   uint32_t* nxt = tmp;
   const size_t gk_step = (size_t)c.L * c.L * 4 * c.n;
@@ -491,10 +493,10 @@ cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uin
     if (e == cudaSuccess) e = set_smem(k_ks_cluster<LG>, smem2);
     if (e != cudaSuccess) return e;
     for (uint32_t j = 0; j < c.logr; j++) {
-      k_ks_digits<LG><<<dim3(count, c.L), ntt_threads(c), smem1, st>>>(c, cur, digits, gal[j]);
+      k_ks_digits<LG><<<dim3(count, c.L), ks_threads, smem1, st>>>(c, cur, digits, gal[j]);
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(c.L, c.L, count);
-      cfg.blockDim = dim3(ntt_threads(c));
+      cfg.blockDim = dim3(ks_threads);
       cfg.dynamicSmemBytes = smem2;
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
