@@ -285,19 +285,27 @@ __global__ void k_mac_reduce(DevCtx c, const uint32_t* __restrict__ partial, int
 // passes need more; smaller rings launch fewer threads and need no bound
 constexpr int ks_min_blocks(int logn) { return logn == 13 ? 3 : logn >= 14 ? 2 : 1; }
 
-// digits[ct][i][:] = INTT_{q_i}(tau_g(c1 limb i)): the RNS digits of the rotated c1
-// as integer polynomials with coefficients in [0, q_i).
+// digits[ct][i][:] = tau_g(INTT_{q_i}(c1 limb i)): the RNS digits of the rotated c1 as
+// integer polynomials with coefficients in [0, q_i).  The automorphism X -> X^g is
+// applied in the coefficient domain at the output (coefficient k moves to k g mod 2n,
+// negated when that is n or more), so the input is read contiguously; the result
+// equals INTT_{q_i} of the NTT-domain permutation of c1.
 template <int LOGN>
 __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
-    k_ks_digits(DevCtx c, const uint32_t* __restrict__ acc,
-                                                   uint32_t* __restrict__ digits, uint32_t gal) {
+    k_ks_digits(DevCtx c, const uint32_t* __restrict__ acc, uint32_t* __restrict__ digits,
+                uint32_t gal) {
   constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   const uint32_t ct = blockIdx.x, i = blockIdx.y;
   const uint32_t* src = acc + ((size_t)(ct * 2 + 1) * c.L + i) * N;
   uint32_t* dst = digits + ((size_t)ct * c.L + i) * N;
-  ntt_inv_io<LOGN>(sm, c.mq[i], [=](uint32_t j) { return __ldg(&src[galois_pos(j, gal, LOGN)]); },
-                   [=](uint32_t k, uint32_t v) { dst[k] = v; });
+  const uint32_t q = c.mq[i].p;
+  ntt_inv_io<LOGN>(sm, c.mq[i], [=](uint32_t j) { return __ldg(&src[j]); },
+                   [=](uint32_t k, uint32_t v) {
+                     const uint32_t e = (k * gal) & (2 * N - 1);
+                     if (e < N) dst[e] = v;
+                     else dst[e - N] = v ? q - v : 0;
+                   });
 }
 
 // Key switch and add, one thread-block cluster of L CTAs per (ciphertext, target limb
@@ -341,11 +349,23 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
   for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[galois_pos(j, gal, LOGN)]);
     uint64_t s1 = __ldg(&c1[j]);
-    for (uint32_t r = 0; r < L; r++) {
-      const uint32_t v = cluster.map_shared_rank(x, r)[padi(j)];
-      const uint32_t* k = gkj + ((size_t)r * L + l) * 4 * N + j;
-      s0 += mulshoup(v, __ldg(k), __ldg(k + N), p);  // each term < 2p
-      s1 += mulshoup(v, __ldg(k + 2 * N), __ldg(k + 3 * N), p);
+    // every rank's loads issued before the first product (L is at most EPHDC_MAXL)
+    uint32_t v[EPHDC_MAXL];
+    uint4 kv[EPHDC_MAXL];
+#pragma unroll
+    for (uint32_t r = 0; r < EPHDC_MAXL; r++) {
+      if (r < L) {
+        v[r] = cluster.map_shared_rank(x, r)[padi(j)];
+        const uint32_t* k = gkj + ((size_t)r * L + l) * 4 * N + j;
+        kv[r] = make_uint4(__ldg(k), __ldg(k + N), __ldg(k + 2 * N), __ldg(k + 3 * N));
+      }
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < EPHDC_MAXL; r++) {
+      if (r < L) {
+        s0 += mulshoup(v[r], kv[r].x, kv[r].y, p);  // each term < 2p
+        s1 += mulshoup(v[r], kv[r].z, kv[r].w, p);
+      }
     }
     o0[j] = red64(s0, p, m.mu);
     o1[j] = red64(s1, p, m.mu);
