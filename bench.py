@@ -602,11 +602,16 @@ def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
         # several groups per model read: a compute-bound multi-group contraction
         macs = G * P * 2 * Kp * L * n
         ach = macs / t / 1e12
-        peak = pk["mac_tps"]
+        peak = alu_peak_tmac(pk)
         return {"kernel": "ptct_mac (multi-group, %d groups)" % G, "bound": "alu",
                 "achieved": ach, "peak": peak, "unit": "Tmodmac/s", "frac": ach / peak,
-                "traffic": None, "peak_source": "measured: register-only 64-bit carry-chain "
-                                                 "multiply-accumulates (ephdc_measure_int_peaks)",
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 64 32-bit integer multiply-adds per clock x "
+                               "%.0f MHz / 2 multiply-adds per 64-bit carry-chain step" %
+                               pk.get("sm_max_mhz", 2070.0),
+                "measured_peak": pk["mac_tps"], "frac_of_measured": ach / pk["mac_tps"],
+                "measured_peak_source": "register-only 64-bit carry-chain multiply-accumulates "
+                                        "(ephdc_measure_int_peaks)",
                 "ms_per_launch": t * 1000.0}
     if dom == "mac":
         model = P * Kp * 2 * L * n * 4
@@ -622,14 +627,16 @@ def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
         # integer-pipe bound: butterflies per second against the issue limit
         bfly = G * P * (L + 1) * (n // 2) * int(math.log2(n))
         ach = bfly / t / 1e12
-        peak = pk["bfly_tps"]
+        peak = alu_peak_tbfly(pk)
         return {"kernel": "encode_plain", "bound": "alu", "achieved": ach,
                 "peak": peak, "unit": "Tbutterfly/s", "frac": ach / peak,
                 "traffic": NCU_TRAFFIC.get((w.name, G, "encode_plain")),
                 "algorithmic_bytes": B * w.D + G * P * L * n * 4,
-                "peak_source": "measured: register-only lazy Shoup butterflies "
-                               "(ephdc_measure_int_peaks); issue-limit estimate %.2f" %
-                               alu_peak_tbfly(pk),
+                "peak_source": "derived: 152 SMs x 128 integer lanes x %.0f MHz / 8 instructions "
+                               "per lazy Shoup butterfly" % pk.get("sm_max_mhz", 2070.0),
+                "measured_peak": pk["bfly_tps"], "frac_of_measured": ach / pk["bfly_tps"],
+                "measured_peak_source": "register-only lazy Shoup butterflies "
+                                        "(ephdc_measure_int_peaks)",
                 "ms_per_launch": t * 1000.0}
     if dom == "hdc_encode":
         ops = 2.0 * B * w.F * w.D
@@ -649,6 +656,13 @@ def alu_peak_tbfly(pk):
     # 5 adds/selects), so the issue-limited rate is lanes x clock / 8
     mhz = pk.get("sm_max_mhz", 2070.0)
     return 152 * 4 * 32 * mhz * 1e6 / 8 / 1e12
+
+
+def alu_peak_tmac(pk):
+    # 152 SMs x 64 32-bit integer multiply-adds per clock (half the 128 lanes); one
+    # 64-bit carry-chain multiply-accumulate is 2 of them (mad.lo.cc, madc.hi)
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    return 152 * 64 * mhz * 1e6 / 2 / 1e12
 
 
 def run_serve(args, w):
