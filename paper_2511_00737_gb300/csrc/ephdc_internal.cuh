@@ -51,6 +51,7 @@ struct DevCtx {
   uint16_t* wh;              // [D][F] fp16 projection
   uint32_t* status;          // nonzero when a bounded device wait gave up
   int32_t ntt_plan;          // pass schedule of the encoding transforms (NttPlan V)
+  int32_t hdc_mode;          // HDC projection: 0 persistent tensor-core GEMM, 1 one tile per CTA
   uint64_t cdt[EPHDC_CDT_LEN];
   uint32_t t;                // plaintext modulus (prime = 1 mod 2n, < 2^30)
   uint32_t rt;               // Q mod t

@@ -943,6 +943,9 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
   } else if (!strcmp(knob, "ntt_plan")) {
     if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "ntt_plan must be 0, 1 or 2");
     c->dc.ntt_plan = (int32_t)v;
+  } else if (!strcmp(knob, "hdc_mode")) {
+    if (v < 0 || v > 1) return fail(c, EPHDC_EINVAL, "hdc_mode must be 0 or 1");
+    c->dc.hdc_mode = (int32_t)v;
   } else if (!strcmp(knob, "mac_tc_min_groups")) {
     if (v < 1) return fail(c, EPHDC_EINVAL, "mac_tc_min_groups must be >= 1");
     c->mac_tc_min_groups = (int)v;
@@ -974,6 +977,7 @@ int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
   if (!strcmp(knob, "mac_min_groups")) return c->mac_min_groups;
   if (!strcmp(knob, "mac_tc_min_groups")) return c->mac_tc_min_groups;
   if (!strcmp(knob, "ntt_plan")) return c->dc.ntt_plan;
+  if (!strcmp(knob, "hdc_mode")) return c->dc.hdc_mode;
   if (!strcmp(knob, "mac_splits")) return c->mac_splits;
   if (!strcmp(knob, "mac_tile"))
     return (int64_t)c->tile.gt * 1000000 + c->tile.ot * 10000 + c->tile.gc * 100 + c->tile.ic;

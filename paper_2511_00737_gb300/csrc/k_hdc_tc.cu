@@ -213,6 +213,169 @@ __global__ void __launch_bounds__(128) k_hdc_tc(const __grid_constant__ CUtensor
                  : "memory");
 }
 
+// Persistent form: a grid of (at most) two CTAs per SM walks the output tiles
+// round-robin.  Six warps with fixed roles:
+//   warp 0 (one lane): TMA producer, streaming the K slices of successive tiles through
+//                      the 3-stage ring without a break at tile boundaries;
+//   warp 1 (one lane): MMA issuer, accumulating tile j in TMEM buffer j % 2 (two
+//                      128-column accumulators);
+//   warps 2..5:        epilogue, each reading its 32 TMEM lanes (lane quarter = warp
+//                      id % 4) of a finished accumulator, quantising and storing, then
+//                      handing the buffer back;
+// so one tile's epilogue overlaps the next tile's MMAs, and the per-tile barrier set-up,
+// TMEM allocation and pipeline fill of the one-tile-per-CTA form are paid once per CTA.
+// Every wait is bounded (status codes 4..7); after a failed wait a role stops issuing,
+// and before TMEM is freed the MMA lane waits, bounded, for its last commit.
+constexpr uint32_t P_TMEM_COLS = 2 * TN;
+constexpr uint32_t P_SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtensorMap ta,
+                                                 const __grid_constant__ CUtensorMap tb, int B,
+                                                 int D, int F, int shift, int bits,
+                                                 int8_t* __restrict__ H, uint32_t* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  // full[S], empty[S], tfull[2], tempty[2], mma_done
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (F + TK - 1) / TK;
+  const int ntn = (D + TN - 1) / TN, ntm = (B + TM - 1) / TM;
+  const int ntiles = ntn * ntm;
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
+  auto tfull = [&](int a) { return smem_u32(&bars[2 * STAGES + a]); };
+  auto tempty = [&](int a) { return smem_u32(&bars[2 * STAGES + 2 + a]); };
+  const uint32_t mma_done = smem_u32(&bars[2 * STAGES + 4]);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; s++) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int a = 0; a < 2; a++) {
+      mbar_init(tfull(a), 1);
+      mbar_init(tempty(a), 4);  // one arrival per epilogue warp
+    }
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(P_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    int it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+      const int m0 = (tile / ntn) * TM, n0 = (tile % ntn) * TN;
+      for (int k = 0; k < nk; k++, it++) {
+        const int s = it % STAGES;
+        if (it >= STAGES && !mbar_wait(empty(s), ((it / STAGES) - 1) & 1, status, 4)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(full(s), STAGE_BYTES);
+        tma_load_2d(smem_u32(sA + s * A_BYTES), &ta, k * TK, m0, full(s));
+        tma_load_2d(smem_u32(sB + s * B_BYTES), &tb, k * TK, n0, full(s));
+      }
+    }
+    // the copies still in flight land before the CTA can exit (complete already unless
+    // a wait above gave up)
+    for (int i = it - STAGES < 0 ? 0 : it - STAGES; i < it; i++)
+      mbar_wait(full(i % STAGES), (i / STAGES) & 1, status, 4);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    int it = 0, j = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, j++) {
+      const int a = j & 1;
+      if (j >= 2 && !mbar_wait(tempty(a), ((j >> 1) - 1) & 1, status, 5)) break;
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(a * TN);
+      for (int k = 0; k < nk; k++, it++) {
+        const int s = it % STAGES;
+        if (!mbar_wait(full(s), (it / STAGES) & 1, status, 6)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < TK / 16; kk++)
+          tc_mma(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), (k | kk) != 0);
+        tc_commit(empty(s));
+      }
+      if (ok) tc_commit(tfull(a));
+    }
+    tc_commit(mma_done);  // arrives when every MMA issued above has completed
+    mbar_wait(mma_done, 0, status, 7);
+  } else if (warp >= 2) {
+    // epilogue: TMEM lane quarter warp % 4 holds rows 32 (warp % 4) .. of the tile
+    const uint32_t q = warp & 3;
+    const int rnd = shift > 0 ? 1 << (shift - 1) : 0;
+    const int lo = -(1 << (bits - 1)), hi = (1 << (bits - 1)) - 1;
+    int j = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, j++) {
+      const int a = j & 1;
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull(a), (j >> 1) & 1, status, 5));
+      if (!ready) break;
+      tc_fence_after();
+      const int m0 = (tile / ntn) * TM, n0 = (tile % ntn) * TN;
+      const int row = m0 + 32 * (int)q + (int)lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t v[32];
+        tc_ld32(tmem + ((32 * q) << 16) + (uint32_t)(a * TN + c0), v);
+        if (c0 + 32 == TN) {
+          // the accumulator is drained: hand it back to the MMA issuer
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty(a));
+        }
+        if (row < B) {
+          int8_t qv[32];
+#pragma unroll
+          for (int e = 0; e < 32; e++) {
+            int x = __float2int_rz(__uint_as_float(v[e]));  // an exact integer
+            x = (x + rnd) >> shift;                          // floor division by 2^s
+            qv[e] = (int8_t)(x < lo ? lo : (x > hi ? hi : x));
+          }
+          const int col = n0 + c0;
+          int8_t* dst = H + (size_t)row * D + col;
+          if (col + 32 <= D && (((uintptr_t)dst) & 15) == 0) {
+            reinterpret_cast<int4*>(dst)[0] = *reinterpret_cast<const int4*>(&qv[0]);
+            reinterpret_cast<int4*>(dst)[1] = *reinterpret_cast<const int4*>(&qv[16]);
+          } else {
+            for (int e = 0; e < 32 && col + e < D; e++) dst[e] = qv[e];
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                 "r"(P_TMEM_COLS)
+                 : "memory");
+}
+
 // int8 -> fp16, 16 elements per thread (n16 chunks of 16)
 __global__ void k_widen(const int8_t* __restrict__ src, __half* __restrict__ dst, size_t n16) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
@@ -298,6 +461,20 @@ cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt
   cudaError_t e = tensor_map(&ta, c.xh, c.F, (uint64_t)B, TM);
   if (e == cudaSuccess) e = tensor_map(&tb, c.wh, c.F, c.D, TN);
   if (e != cudaSuccess) return e;
+  const int tiles = (int)((c.D + TN - 1) / TN) * ((B + TM - 1) / TM);
+  if (c.hdc_mode == 0) {
+    // persistent: at most two CTAs per SM
+    static int sms = 0;
+    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
+      return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k_hdc_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             P_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    const int grid = tiles < 2 * sms ? tiles : 2 * sms;
+    k_hdc_tcp<<<grid, 192, P_SMEM_BYTES, st>>>(ta, tb, B, (int)c.D, (int)c.F, c.shift,
+                                               (int)c.bits, H, c.status);
+    return cudaGetLastError();
+  }
   e = cudaFuncSetAttribute(k_hdc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid((c.D + TN - 1) / TN, (B + TM - 1) / TM);

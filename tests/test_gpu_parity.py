@@ -109,15 +109,21 @@ def test_hdc_encode_matches_oracle(small):
     assert np.array_equal(small.g_H.cpu().numpy(), small.H)
 
 
+@pytest.mark.parametrize("mode", [0, 1])  # persistent GEMM, one tile per CTA
 @pytest.mark.parametrize("B,D,F,bits,shift", [(1, 257, 16, 8, 0), (300, 1000, 96, 4, 6),
-                                              (129, 130, 608, 8, 5), (2000, 64, 1024, 2, 9)])
-def test_hdc_encode_ragged_shapes(B, D, F, bits, shift):
+                                              (129, 130, 608, 8, 5), (2000, 64, 1024, 2, 9),
+                                              (8000, 1200, 608, 8, 5)])
+def test_hdc_encode_ragged_shapes(B, D, F, bits, shift, mode):
+    """Ragged rows and columns; the last shape has 630 output tiles, so each persistent
+    CTA (two per SM) takes two or three tiles and reuses its TMEM accumulators."""
     ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
+    ctx.tune_set("hdc_mode", mode)
     X = WL.features(B + D, B, F)
     Wt = WL.projection(B + D, D, F)
     X[0] = 127
     H = ctx.hdc_encode(_dev(X), _dev(Wt))
     assert np.array_equal(H.cpu().numpy(), O.hdc_encode(X, Wt, shift, bits))
+    ctx.device_status()
     ctx.close()
 
 
@@ -130,8 +136,9 @@ def test_hdc_encode_extreme_magnitudes_exact():
     X[:64] = 127
     Wt[:100] = -1
     Wt[100:200] = 1
-    for shift, bits in [(0, 8), (10, 8), (14, 4)]:
+    for shift, bits, mode in [(0, 8, 0), (10, 8, 1), (14, 4, 0)]:
         ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
+        ctx.tune_set("hdc_mode", mode)
         H = ctx.hdc_encode(_dev(X), _dev(Wt))
         assert np.array_equal(H.cpu().numpy(), O.hdc_encode(X, Wt, shift, bits))
         ctx.device_status()
