@@ -49,6 +49,8 @@ def parse():
                     help="streams (contexts) that consecutive batches alternate over")
     ap.add_argument("--mac-mode", type=int, default=-1,
                     help="force the multiply-accumulate schedule (profiling)")
+    ap.add_argument("--hdc-mode", type=int, default=-1,
+                    help="force the HDC projection kernel (library default otherwise)")
     ap.add_argument("--pack", type=int, default=0,
                     help="consecutive batches packed into one step (one model stream); "
                          "0 = as many as fit in 16 query groups")
@@ -228,6 +230,8 @@ def run_ours(args, w, B):
     ctx = E.Context.for_workload(w, max_batch=(-(-B // cap) * cap) if multi else B)
     if args.mac_mode >= 0:
         ctx.tune_set("mac_mode", args.mac_mode)
+    if args.hdc_mode >= 0:
+        ctx.tune_set("hdc_mode", args.hdc_mode)
     sk, gk = ctx.keygen(seed)
     cls = torch.from_numpy(WL.classes(seed, w.k, w.D)).to(dev)
     model = ctx.encrypt_model(cls, sk, seed)
@@ -271,6 +275,8 @@ def run_ours(args, w, B):
         for cx in ctxs[1:]:
             if tuned:
                 AT.apply(cx, tuned)
+            if args.hdc_mode >= 0:
+                cx.tune_set("hdc_mode", args.hdc_mode)
         outs = [out] + [cx.out_ct(B) for cx in ctxs[1:]]
         streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
 

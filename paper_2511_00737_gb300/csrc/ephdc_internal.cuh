@@ -51,7 +51,9 @@ struct DevCtx {
   uint16_t* wh;              // [D][F] fp16 projection
   uint32_t* status;          // nonzero when a bounded device wait gave up
   int32_t ntt_plan;          // pass schedule of the encoding transforms (NttPlan V)
-  int32_t hdc_mode;          // HDC projection: 0 persistent tensor-core GEMM, 1 one tile per CTA
+  int32_t hdc_mode;          // HDC projection: 0 persistent GEMM with 128 x 256 tiles and
+                             // a 3-stage ring, 1 one 128 x 128 tile per CTA, 2 persistent
+                             // with 128 x 128 tiles, 3 as 0 with a 4-stage ring
   uint64_t cdt[EPHDC_CDT_LEN];
   uint32_t t;                // plaintext modulus (prime = 1 mod 2n, < 2^30)
   uint32_t rt;               // Q mod t

@@ -33,7 +33,10 @@ constexpr uint32_t TMEM_COLS = TN;  // fp32 accumulator: 128 lanes x 128 columns
 
 // instruction descriptor, kind::f16: D = f32 (bits 4-5 = 1), A = B = f16 (bits 7-9,
 // 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+constexpr uint32_t idesc_f16(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+constexpr uint32_t IDESC = idesc_f16(TN);
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -88,11 +91,12 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc,
+                                       uint32_t idesc = IDESC) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -213,12 +217,13 @@ __global__ void __launch_bounds__(128) k_hdc_tc(const __grid_constant__ CUtensor
                  : "memory");
 }
 
-// Persistent form: a grid of (at most) two CTAs per SM walks the output tiles
-// round-robin.  Six warps with fixed roles:
+// Persistent form: a grid of (at most) one CTA per SM with 128 x 256 output tiles (two
+// 256-column accumulators fill the SM's TMEM; a ring of 48 KB stages), or two CTAs per
+// SM with 128 x 128 tiles, walks the output tiles round-robin.  Six warps with fixed
+// roles:
 //   warp 0 (one lane): TMA producer, streaming the K slices of successive tiles through
 //                      the 3-stage ring without a break at tile boundaries;
-//   warp 1 (one lane): MMA issuer, accumulating tile j in TMEM buffer j % 2 (two
-//                      128-column accumulators);
+//   warp 1 (one lane): MMA issuer, accumulating tile j in TMEM buffer j % 2;
 //   warps 2..5:        epilogue, each reading its 32 TMEM lanes (lane quarter = warp
 //                      id % 4) of a finished accumulator, quantising and storing, then
 //                      handing the buffer back;
@@ -226,17 +231,27 @@ __global__ void __launch_bounds__(128) k_hdc_tc(const __grid_constant__ CUtensor
 // TMEM allocation and pipeline fill of the one-tile-per-CTA form are paid once per CTA.
 // Every wait is bounded (status codes 4..7); after a failed wait a role stops issuing,
 // and before TMEM is freed the MMA lane waits, bounded, for its last commit.
-constexpr uint32_t P_TMEM_COLS = 2 * TN;
-constexpr uint32_t P_SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+template <int PN, int PS>
+struct PersistentShape {
+  static constexpr uint32_t B_BYTES = PN * TK * 2;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t TMEM_COLS = 2 * PN;  // two accumulators
+  static constexpr uint32_t SMEM = PS * STAGE + 1024 + 256;
+};
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
+template <int PN, int PS>
 __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtensorMap ta,
                                                  const __grid_constant__ CUtensorMap tb, int B,
                                                  int D, int F, int shift, int bits,
                                                  int8_t* __restrict__ H, uint32_t* status) {
+  using Sh = PersistentShape<PN, PS>;
+  constexpr int STAGES = PS, TN = PN;
+  constexpr uint32_t B_BYTES = Sh::B_BYTES, STAGE_BYTES = Sh::STAGE;
+  constexpr uint32_t IDESC_P = idesc_f16(PN);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -269,7 +284,7 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(P_TMEM_COLS)
+                 "r"(Sh::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -318,7 +333,8 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
         const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
         for (int kk = 0; kk < TK / 16; kk++)
-          tc_mma(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), (k | kk) != 0);
+          tc_mma(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), (k | kk) != 0,
+                 IDESC_P);
         tc_commit(empty(s));
       }
       if (ok) tc_commit(tfull(a));
@@ -372,7 +388,7 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
-                 "r"(P_TMEM_COLS)
+                 "r"(Sh::TMEM_COLS)
                  : "memory");
 }
 
@@ -461,19 +477,32 @@ cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt
   cudaError_t e = tensor_map(&ta, c.xh, c.F, (uint64_t)B, TM);
   if (e == cudaSuccess) e = tensor_map(&tb, c.wh, c.F, c.D, TN);
   if (e != cudaSuccess) return e;
-  const int tiles = (int)((c.D + TN - 1) / TN) * ((B + TM - 1) / TM);
-  if (c.hdc_mode == 0) {
-    // persistent: at most two CTAs per SM
+  if (c.hdc_mode != 1) {
+    // persistent: 128 x 256 tiles with all 512 TMEM columns, one CTA per SM, and a
+    // 3-stage ring of 145 KB that leaves room on the SM for an encoder CTA of another
+    // stream (mode 0) or a 4-stage ring of 193 KB (mode 3); or 128 x 128 tiles, two
+    // CTAs per SM (mode 2)
     static int sms = 0;
     if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
       return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(k_hdc_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             P_SMEM_BYTES);
+    const bool wide = c.hdc_mode != 2;
+    const int pn = wide ? 256 : 128;
+    if (wide) e = tensor_map(&tb, c.wh, c.F, c.D, 256);
     if (e != cudaSuccess) return e;
-    const int grid = tiles < 2 * sms ? tiles : 2 * sms;
-    k_hdc_tcp<<<grid, 192, P_SMEM_BYTES, st>>>(ta, tb, B, (int)c.D, (int)c.F, c.shift,
-                                               (int)c.bits, H, c.status);
-    return cudaGetLastError();
+    const int tiles = (int)((c.D + pn - 1) / pn) * ((B + TM - 1) / TM);
+    const int per_sm = wide ? 1 : 2;
+    const int grid = tiles < per_sm * sms ? tiles : per_sm * sms;
+    auto launch = [&](auto kern, uint32_t smem_bytes) -> cudaError_t {
+      cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           smem_bytes);
+      if (r != cudaSuccess) return r;
+      kern<<<grid, 192, smem_bytes, st>>>(ta, tb, B, (int)c.D, (int)c.F, c.shift, (int)c.bits, H,
+                                          c.status);
+      return cudaGetLastError();
+    };
+    if (c.hdc_mode == 0) return launch(k_hdc_tcp<256, 3>, PersistentShape<256, 3>::SMEM);
+    if (c.hdc_mode == 3) return launch(k_hdc_tcp<256, 4>, PersistentShape<256, 4>::SMEM);
+    return launch(k_hdc_tcp<128, 3>, PersistentShape<128, 3>::SMEM);
   }
   e = cudaFuncSetAttribute(k_hdc_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;

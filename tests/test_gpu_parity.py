@@ -109,7 +109,7 @@ def test_hdc_encode_matches_oracle(small):
     assert np.array_equal(small.g_H.cpu().numpy(), small.H)
 
 
-@pytest.mark.parametrize("mode", [0, 1])  # persistent GEMM, one tile per CTA
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])  # persistent 128x256 (3 / 4 stages: 0 / 3), one tile per CTA, persistent 128x128
 @pytest.mark.parametrize("B,D,F,bits,shift", [(1, 257, 16, 8, 0), (300, 1000, 96, 4, 6),
                                               (129, 130, 608, 8, 5), (2000, 64, 1024, 2, 9),
                                               (8000, 1200, 608, 8, 5)])
@@ -136,7 +136,7 @@ def test_hdc_encode_extreme_magnitudes_exact():
     X[:64] = 127
     Wt[:100] = -1
     Wt[100:200] = 1
-    for shift, bits, mode in [(0, 8, 0), (10, 8, 1), (14, 4, 0)]:
+    for shift, bits, mode in [(0, 8, 0), (10, 8, 1), (14, 4, 2)]:
         ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
         ctx.tune_set("hdc_mode", mode)
         H = ctx.hdc_encode(_dev(X), _dev(Wt))
