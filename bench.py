@@ -51,6 +51,8 @@ def parse():
                     help="force the multiply-accumulate schedule (profiling)")
     ap.add_argument("--hdc-mode", type=int, default=-1,
                     help="force the HDC projection kernel (library default otherwise)")
+    ap.add_argument("--mac-tile", type=int, default=-1,
+                    help="force the tiled multiply-accumulate with this tiling (profiling)")
     ap.add_argument("--pack", type=int, default=0,
                     help="consecutive batches packed into one step (one model stream); "
                          "0 = as many as fit in 16 query groups")
@@ -260,7 +262,10 @@ def run_ours(args, w, B):
         from paper_2511_00737_gb300 import autotune as AT
         H0 = ctx.hdc_encode(Xd[0], Wt)
         tuned, _, _ = AT.tune_encode(ctx, H0, reps=5)  # pass schedule of the transforms
-        if ctx.groups(B) >= 2 and args.mac_mode < 0:
+        if args.mac_tile >= 0:
+            tuned = {**tuned, "mac_mode": 2, "mac_tile": args.mac_tile}
+            AT.apply(ctx, tuned)
+        elif ctx.groups(B) >= 2 and args.mac_mode < 0:
             # several groups share each model read: let the autotuner pick the schedule
             pt0 = ctx.encode_plain(H0)
             mac, _, _ = AT.tune_similarity(ctx, pt0, B, model, gk, reps=2)
