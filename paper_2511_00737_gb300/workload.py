@@ -104,6 +104,10 @@ def config(name, **over):
         "clients64": dict(n=8192, L=4, k=7, k_in=1, r=8, D=10000, F=768, bits=4, B=0),
         # 65536 queries, F=1024, D=16384, 8-bit HVs, 16 classes, n=16384, 6 primes
         "dense65536": dict(n=16384, L=6, k=16, k_in=1, r=16, D=16384, F=1024, bits=8, B=65536),
+        # the same batch with r = 8: 32 groups of 2048 queries, P = 2048 (a 25.8 GB
+        # model), 3 rotations on half as many ciphertexts
+        "dense65536_r8": dict(n=16384, L=6, k=16, k_in=1, r=8, D=16384, F=1024, bits=8,
+                              B=65536),
         # serving: F=608, D=10000, 7 classes, n=8192, 4 primes
         "serve": dict(n=8192, L=4, k=7, k_in=1, r=8, D=10000, F=608, bits=8, B=0),
     }[name]
