@@ -300,7 +300,16 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
   const uint32_t* src = acc + ((size_t)(ct * 2 + 1) * c.L + i) * N;
   uint32_t* dst = digits + ((size_t)ct * c.L + i) * N;
   const uint32_t q = c.mq[i].p;
-  ntt_inv_io<LOGN>(sm, c.mq[i], [=](uint32_t j) { return __ldg(&src[j]); },
+  // coalesced 16-byte loads into the padded buffer (the first inverse pass reads 32
+  // consecutive words per thread, which straight from global memory would be strided)
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
+    const uint4 v = __ldg(&s4[k]);
+    sm[padi(4 * k)] = v.x; sm[padi(4 * k + 1)] = v.y; sm[padi(4 * k + 2)] = v.z;
+    sm[padi(4 * k + 3)] = v.w;
+  }
+  __syncthreads();
+  ntt_inv_io<LOGN>(sm, c.mq[i], SmemLd{sm},
                    [=](uint32_t k, uint32_t v) {
                      const uint32_t e = (k * gal) & (2 * N - 1);
                      if (e < N) dst[e] = v;
