@@ -317,62 +317,68 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
                    });
 }
 
-// Key switch and add, one thread-block cluster of L CTAs per (ciphertext, target limb
-// l); cluster rank i owns RNS digit i and holds X_i = NTT_l(d_i) in its shared memory
-// (for i = l the digit's transform is tau(acc1 limb l) itself, read directly).  Rank i
-// then produces its 1/L slice of the coefficients, reading every rank's X_r through
-// distributed shared memory and multiplying by that rank's key parts:
-//   out[ct][0][l] = acc0 + tau(acc0) + sum_r X_r * k0[r][l],
-//   out[ct][1][l] = acc1 + sum_r X_r * k1[r][l].
+// Key switch and add, one thread-block cluster of L - 1 CTAs per (ciphertext, target
+// limb l).  Cluster rank i owns RNS digit d = i (i < l) or i + 1 (i >= l) and holds
+// X_d = NTT_l(d-th digit) in its shared memory; the digit l needs no transform, its
+// NTT_l is tau(acc1 limb l) itself.  Rank i then produces its 1/(L - 1) slice of the
+// coefficients, reading every rank's X_d through distributed shared memory and
+// tau(acc1 limb l) from global memory, each multiplied by its key parts:
+//   out[ct][0][l] = acc0 + tau(acc0) + sum_d X_d * k0[d][l],
+//   out[ct][1][l] = acc1 + sum_d X_d * k1[d][l].
 // One transform buffer per CTA (the products are formed in the reduction).
 // gkj: [L digits][L limbs][4][n] = (k0, k0 Shoup, k1, k1 Shoup), NTT domain.
 template <int LOGN>
 __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
     k_ks_cluster(DevCtx c, const uint32_t* __restrict__ acc,
-                                                    const uint32_t* __restrict__ digits,
-                                                    const uint32_t* __restrict__ gkj,
-                                                    uint32_t* __restrict__ out, uint32_t gal) {
+                 const uint32_t* __restrict__ digits, const uint32_t* __restrict__ gkj,
+                 uint32_t* __restrict__ out, uint32_t gal) {
   constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   uint32_t* x = sm;  // padded transform buffer
   cg::cluster_group cluster = cg::this_cluster();
   const uint32_t i = blockIdx.x, l = blockIdx.y, ct = blockIdx.z;
+  const uint32_t L = c.L, R = L - 1;  // cluster ranks
   const ModP m = c.mq[l];
   const uint32_t p = m.p;
   const uint32_t* c1 = acc + ((size_t)(ct * 2 + 1) * c.L + l) * N;
-  if (i == l) {
-    for (uint32_t j = threadIdx.x; j < N; j += blockDim.x)
-      x[padi(j)] = __ldg(&c1[galois_pos(j, gal, LOGN)]);
-  } else {
-    const uint32_t* dg = digits + ((size_t)ct * c.L + i) * N;
+  {
+    const uint32_t d = i < l ? i : i + 1;
+    const uint32_t* dg = digits + ((size_t)ct * c.L + d) * N;
     ntt_fwd_io<LOGN>(x, m, [=](uint32_t kk) { return csub(__ldg(&dg[kk]), p); },  // d < 2 q_l
                      SmemSt{x});
   }
   cluster.sync();
-  const uint32_t L = c.L;
-  const uint32_t slice = (N + L - 1) / L;
+  const uint32_t slice = (N + R - 1) / R;
   const uint32_t j0 = i * slice, j1 = min(N, j0 + slice);
   const uint32_t* c0 = acc + ((size_t)(ct * 2 + 0) * c.L + l) * N;
   uint32_t* o0 = out + ((size_t)(ct * 2 + 0) * c.L + l) * N;
   uint32_t* o1 = out + ((size_t)(ct * 2 + 1) * c.L + l) * N;
+  const uint32_t* kl = gkj + ((size_t)l * L + l) * 4 * N;  // key parts of digit l
   for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[galois_pos(j, gal, LOGN)]);
+    const uint32_t gp = galois_pos(j, gal, LOGN);
+    uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[gp]);
     uint64_t s1 = __ldg(&c1[j]);
     // every rank's loads issued before the first product (L is at most EPHDC_MAXL)
-    uint32_t v[EPHDC_MAXL];
-    uint4 kv[EPHDC_MAXL];
+    const uint32_t vl = __ldg(&c1[gp]);
+    const uint4 kvl = make_uint4(__ldg(kl + j), __ldg(kl + N + j), __ldg(kl + 2 * N + j),
+                                 __ldg(kl + 3 * N + j));
+    uint32_t v[EPHDC_MAXL - 1];
+    uint4 kv[EPHDC_MAXL - 1];
 #pragma unroll
-    for (uint32_t r = 0; r < EPHDC_MAXL; r++) {
-      if (r < L) {
+    for (uint32_t r = 0; r < EPHDC_MAXL - 1; r++) {
+      if (r < R) {
+        const uint32_t d = r < l ? r : r + 1;
         v[r] = cluster.map_shared_rank(x, r)[padi(j)];
-        const uint32_t* k = gkj + ((size_t)r * L + l) * 4 * N + j;
+        const uint32_t* k = gkj + ((size_t)d * L + l) * 4 * N + j;
         kv[r] = make_uint4(__ldg(k), __ldg(k + N), __ldg(k + 2 * N), __ldg(k + 3 * N));
       }
     }
+    s0 += mulshoup(vl, kvl.x, kvl.y, p);  // each term < 2p
+    s1 += mulshoup(vl, kvl.z, kvl.w, p);
 #pragma unroll
-    for (uint32_t r = 0; r < EPHDC_MAXL; r++) {
-      if (r < L) {
-        s0 += mulshoup(v[r], kv[r].x, kv[r].y, p);  // each term < 2p
+    for (uint32_t r = 0; r < EPHDC_MAXL - 1; r++) {
+      if (r < R) {
+        s0 += mulshoup(v[r], kv[r].x, kv[r].y, p);
         s1 += mulshoup(v[r], kv[r].z, kv[r].w, p);
       }
     }
@@ -524,13 +530,13 @@ cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uin
     for (uint32_t j = 0; j < c.logr; j++) {
       k_ks_digits<LG><<<dim3(count, c.L), ks_threads, smem1, st>>>(c, cur, digits, gal[j]);
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(c.L, c.L, count);
+      cfg.gridDim = dim3(c.L - 1, c.L, count);
       cfg.blockDim = dim3(ks_threads);
       cfg.dynamicSmemBytes = smem2;
       cfg.stream = st;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = c.L;
+      attr[0].val.clusterDim.x = c.L - 1;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
