@@ -647,7 +647,7 @@ ephdc_status hdc_encode(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_t
   CHECK_B(c, B);
   cudaError_t e;
   {
-    StageTimer tm(c, EPHDC_STAGE_HDC, (cudaStream_t)stream, 1);
+    StageTimer tm(c, EPHDC_STAGE_HDC, (cudaStream_t)stream, 3);  // widen X, widen Wt, GEMM
     e = ephdc::launch_hdc_encode(c->dc, X, Wt, B, H, (cudaStream_t)stream);
   }
   return launched(c, e, "hdc_encode");
@@ -661,7 +661,7 @@ ephdc_status bfv_encode_plain(ephdc_ctx* c, const int8_t* H, int32_t B, uint32_t
   CHECK_B(c, B);
   cudaError_t e;
   {
-    StageTimer tm(c, EPHDC_STAGE_ENCODE, (cudaStream_t)stream, 1);
+    StageTimer tm(c, EPHDC_STAGE_ENCODE, (cudaStream_t)stream, c->dc.scale_g ? 2 : 1);
     e = ephdc::launch_encode_plain(c->dc, H, B, pt, (cudaStream_t)stream);
   }
   return launched(c, e, "encode_plain");
@@ -799,12 +799,12 @@ ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   {
-    StageTimer tm(c, EPHDC_STAGE_HDC, st, 1);
+    StageTimer tm(c, EPHDC_STAGE_HDC, st, 3);  // widen X, widen Wt, GEMM
     e = ephdc::launch_hdc_encode(c->dc, X, Wt, B, c->H, st);
   }
   if (e != cudaSuccess) return launched(c, e, "hdc_encode");
   {
-    StageTimer tm(c, EPHDC_STAGE_ENCODE, st, 1);
+    StageTimer tm(c, EPHDC_STAGE_ENCODE, st, c->dc.scale_g ? 2 : 1);
     e = ephdc::launch_encode_plain(c->dc, c->H, B, c->pt, st);
   }
   if (e != cudaSuccess) return launched(c, e, "encode_plain");
@@ -908,7 +908,8 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* c, const ephdc_request* reqs, int32_t 
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   {
-    StageTimer tm(c, EPHDC_STAGE_HDC, st, (uint64_t)((nreq + 63) / 64) + 3);
+    // one gather per 64 requests, then widen Wt and the GEMM
+    StageTimer tm(c, EPHDC_STAGE_HDC, st, (uint64_t)((nreq + 63) / 64) + 2);
     int32_t row = 0;
     for (int32_t r0 = 0; r0 < nreq && e == cudaSuccess; r0 += 64) {
       ephdc::GatherTable t;
@@ -925,7 +926,7 @@ ephdc_status ephdc_infer_multi(ephdc_ctx* c, const ephdc_request* reqs, int32_t 
   }
   if (e != cudaSuccess) return launched(c, e, "hdc_encode");
   {
-    StageTimer tm(c, EPHDC_STAGE_ENCODE, st, 1);
+    StageTimer tm(c, EPHDC_STAGE_ENCODE, st, c->dc.scale_g ? 2 : 1);
     e = ephdc::launch_encode_plain(c->dc, c->H, (int)total, c->pt, st);
   }
   if (e != cudaSuccess) return launched(c, e, "encode_plain");

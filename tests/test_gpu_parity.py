@@ -304,3 +304,47 @@ def test_query_row_pack_matches_oracle(r, k_in, D, B):
     got = ctx.plain_to_host_coeff(pt, G * o.P)
     assert np.array_equal(got, _lifted(m.reshape(G * o.P, w.n), o.q))
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["small", "face1024"])
+def test_launch_count_matches_profiler(name):
+    """The library's own kernel-launch count for one fused call (the figure bench.py
+    reports as gpu_launches) equals the number of this library's kernels a CUDA
+    activity trace sees."""
+    w = WL.config(name)
+    ctx = E.Context.for_workload(w)
+    X = _dev(WL.features(w.seed, w.B, w.F))
+    Wt = _dev(WL.projection(w.seed, w.D, w.F))
+    sk, gk = ctx.keygen(w.seed)
+    model = ctx.encrypt_model(_dev(WL.classes(w.seed, w.k, w.D)), sk, w.seed)
+    ctx.infer(X, Wt, model, gk)  # first call: lazy set-up outside the trace
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read()
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]):  # the first session may come up late
+        torch.zeros(1, device="cuda").add_(1)
+        torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        ctx.infer(X, Wt, model, gk)
+        torch.cuda.synchronize()
+    _, _, claimed = ctx.profile_read()
+    ctx.profile(False)
+    # raw activity records: kernels launched outside torch ops have no CPU-side parent
+    raw = []
+    try:
+        for e in prof.profiler.kineto_results.events():
+            raw.append((e.name(), str(e.device_type())))
+    except AttributeError:
+        raw = [(e.name, str(e.device_type)) for e in prof.events()]
+
+    def ours(n):
+        for pre in ("void ", "(anonymous namespace)::", "<unnamed>::", "ephdc::"):
+            n = n.replace(pre, "")
+        return n.startswith("k_")
+    names = [n for n, d in raw if "CUDA" in d and ours(n)]
+    if not names:
+        pytest.skip("the CUDA activity trace recorded none of this library's kernels "
+                    "(%d records, e.g. %s)" % (len(raw), raw[:3]))
+    assert claimed == len(names), sorted(set(names))
+    ctx.close()
