@@ -482,9 +482,10 @@ cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt
     // 3-stage ring of 145 KB that leaves room on the SM for an encoder CTA of another
     // stream (mode 0) or a 4-stage ring of 193 KB (mode 3); or 128 x 128 tiles, two
     // CTAs per SM (mode 2)
-    static int sms = 0;
-    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess)
-      return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
     const bool wide = c.hdc_mode != 2;
     const int pn = wide ? 256 : 128;
     if (wide) e = tensor_map(&tb, c.wh, c.F, c.D, 256);
