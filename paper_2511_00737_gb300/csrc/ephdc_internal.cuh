@@ -326,60 +326,51 @@ __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP&
   // the contiguous pass of a full-size transform reads the transposed twiddle copy
   constexpr bool CONTIG = S == 1 && K == 5;
   const uint32_t p = m.p, two_p = 2 * p;
-  for (uint32_t gi = threadIdx.x; gi < GROUPS; gi += blockDim.x) {
+  const uint2* twl = FWD ? m.twl : m.itwl;
+  // (this loop form, a signed iteration count with an exit test and one stage loop for
+  // both directions, compiles to fewer live registers than a strided group index)
+  for (int itx = 0; itx < (1 << 30); itx++) {
+    const uint32_t gi = threadIdx.x + itx * blockDim.x;
+    if (gi >= GROUPS) break;
     const uint32_t blk = gi >> LOGS, j0 = gi & (S - 1);
     const uint32_t base = (blk << (LOGS + K)) + j0;
+    auto twa = [&](int r, int u) -> const uint2* {
+      return CONTIG ? &twl[((1u << r) - 1 + u) * M0 + blk] : &tw[((M0 + blk) << r) + u];
+    };
     uint32_t x[1 << K];
 #pragma unroll
     for (int e = 0; e < (1 << K); e++) x[e] = ld(base + e * S);
-    if (FWD) {
 #pragma unroll
-      for (int r = 0; r < K; r++) {
-        const int half = 1 << (K - 1 - r);
-        uint2 w[1 << (K - 1)];
+    for (int rr = 0; rr < K; rr++) {
+      const int r = FWD ? rr : K - 1 - rr;
+      const int half = 1 << (K - 1 - r);
+      uint2 w[1 << (K - 1)];
 #pragma unroll
-        for (int u = 0; u < (1 << r); u++)
-          w[u] = CONTIG ? __ldg(&m.twl[((1u << r) - 1 + u) * M0 + blk])
-                        : __ldg(&tw[((M0 + blk) << r) + u]);
+      for (int u = 0; u < (1 << r); u++) w[u] = __ldg(twa(r, u));
 #pragma unroll
-        for (int e = 0; e < (1 << K); e++) {
-          if (e & half) continue;
-          const uint2 ww = w[e >> (K - r)];
+      for (int e = 0; e < (1 << K); e++) {
+        if (e & half) continue;
+        const uint2 ww = w[e >> (K - r)];
+        if (FWD) {
           const uint32_t X = min(x[e], x[e] - two_p);
           const uint32_t T = mulshoup(x[e + half], ww.x, ww.y, p);
           x[e] = X + T;
           x[e + half] = X - T + two_p;
-        }
-      }
-      if (FINAL) {
-#pragma unroll
-        for (int e = 0; e < (1 << K); e++) {
-          const uint32_t v = min(x[e], x[e] - two_p);
-          x[e] = min(v, v - p);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int r = K - 1; r >= 0; r--) {
-        const int half = 1 << (K - 1 - r);
-        uint2 w[1 << (K - 1)];
-#pragma unroll
-        for (int u = 0; u < (1 << r); u++)
-          w[u] = CONTIG ? __ldg(&m.itwl[((1u << r) - 1 + u) * M0 + blk])
-                        : __ldg(&tw[((M0 + blk) << r) + u]);
-#pragma unroll
-        for (int e = 0; e < (1 << K); e++) {
-          if (e & half) continue;
-          const uint2 ww = w[e >> (K - r)];
+        } else {
           const uint32_t X = x[e], Y = x[e + half];
           const uint32_t U = X + Y;
           x[e] = min(U, U - two_p);
           x[e + half] = mulshoup(X - Y + two_p, ww.x, ww.y, p);
         }
       }
-      if (FINAL) {
+    }
+    if (FINAL) {
 #pragma unroll
-        for (int e = 0; e < (1 << K); e++) {
+      for (int e = 0; e < (1 << K); e++) {
+        if (FWD) {
+          const uint32_t v = min(x[e], x[e] - two_p);
+          x[e] = min(v, v - p);
+        } else {
           const uint32_t v = mulshoup(x[e], m.ninv, m.ninv_sh, p);
           x[e] = min(v, v - p);
         }
