@@ -306,13 +306,27 @@ struct NttPlan {
 // Shared-memory element access (padded layout); the first pass of a transform may
 // take a custom loader and the last pass a custom storer, so that the producer
 // (slot gather, lift) and the consumer (global store) fuse into the passes.
+// A loader or storer that also takes the padded index directly (`at`) lets a pass form
+// each element's address as one padded base plus a compile-time offset.
 struct SmemLd {
+  static constexpr bool kPadded = true;
   const uint32_t* s;
   __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return s[padi(i)]; }
+  __device__ __forceinline__ uint32_t at(uint32_t pi) const { return s[pi]; }
 };
 struct SmemSt {
+  static constexpr bool kPadded = true;
   uint32_t* s;
   __device__ __forceinline__ void operator()(uint32_t i, uint32_t v) const { s[padi(i)] = v; }
+  __device__ __forceinline__ void at(uint32_t pi, uint32_t v) const { s[pi] = v; }
+};
+template <class F, class = void>
+struct PaddedAccess {
+  static constexpr bool value = false;
+};
+template <class F>
+struct PaddedAccess<F, decltype((void)F::kPadded)> {
+  static constexpr bool value = F::kPadded;
 };
 
 // FINAL: forward -> reduce outputs to [0, p); inverse -> multiply by n^-1, reduce
@@ -338,8 +352,17 @@ __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP&
       return CONTIG ? &twl[((1u << r) - 1 + u) * M0 + blk] : &tw[((M0 + blk) << r) + u];
     };
     uint32_t x[1 << K];
+    // padded index of element e = padi(base) + e PS, exactly: a contiguous pass has a
+    // 32-aligned base, a strided one adds multiples of 32
+    constexpr uint32_t PS = S == 1 ? 1 : S + S / 32;
+    if constexpr (PaddedAccess<LD>::value) {
+      const uint32_t pb = padi(base);
 #pragma unroll
-    for (int e = 0; e < (1 << K); e++) x[e] = ld(base + e * S);
+      for (int e = 0; e < (1 << K); e++) x[e] = ld.at(pb + e * PS);
+    } else {
+#pragma unroll
+      for (int e = 0; e < (1 << K); e++) x[e] = ld(base + e * S);
+    }
 #pragma unroll
     for (int rr = 0; rr < K; rr++) {
       const int r = FWD ? rr : K - 1 - rr;
@@ -376,8 +399,14 @@ __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP&
         }
       }
     }
+    if constexpr (PaddedAccess<ST>::value) {
+      const uint32_t pb = padi(base);
 #pragma unroll
-    for (int e = 0; e < (1 << K); e++) st(base + e * S, x[e]);
+      for (int e = 0; e < (1 << K); e++) st.at(pb + e * PS, x[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < (1 << K); e++) st(base + e * S, x[e]);
+    }
   }
 }
 

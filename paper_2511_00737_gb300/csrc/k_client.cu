@@ -23,6 +23,18 @@ __device__ __forceinline__ uint32_t galois_pos(uint32_t j, uint32_t g, uint32_t 
 }
 
 // ------------------------------------------------------------------ EncPt
+// centred lift of a coefficient in [0, t) into Z_{q_l}: v, or v + q_l - t above t/2
+struct CentredLift {
+  static constexpr bool kPadded = true;
+  const uint32_t* s;
+  uint32_t thalf, p_minus_t;
+  __device__ __forceinline__ uint32_t at(uint32_t pi) const {
+    const uint32_t v = s[pi];
+    return v <= thalf ? v : v + p_minus_t;
+  }
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return at(padi(i)); }
+};
+
 // One CTA per plaintext (g, i).  The query slots are packed (pack_query_slots), the
 // inverse NTT mod t gives the plaintext coefficients, and for each limb the centred
 // lift feeds the forward NTT, whose output is staged in shared memory and stored
@@ -49,12 +61,8 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
   const uint32_t t = c.t, thalf = (t - 1) / 2;
   for (uint32_t l = 0; l < c.L; l++) {
     const ModP m = c.mq[l];
-    const uint32_t p = m.p;
-    auto lift = [=](uint32_t k) -> uint32_t {
-      const uint32_t v = mb[padi(k)];
-      return v <= thalf ? v : v + p - t;  // centred lift into Z_{q_l}
-    };
-    ntt_fwd_io<LOGN, decltype(lift), SmemSt, V>(wb, m, lift, SmemSt{wb});
+    const CentredLift lift{mb, thalf, m.p - t};
+    ntt_fwd_io<LOGN, CentredLift, SmemSt, V>(wb, m, lift, SmemSt{wb});
     uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
     for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
       dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
