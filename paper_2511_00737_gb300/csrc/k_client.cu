@@ -64,9 +64,10 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
     const CentredLift lift{mb, thalf, m.p - t};
     ntt_fwd_io<LOGN, CentredLift, SmemSt, V>(wb, m, lift, SmemSt{wb});
     uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
-    for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x)
-      dst[k] = make_uint4(wb[padi(4 * k)], wb[padi(4 * k + 1)], wb[padi(4 * k + 2)],
-                          wb[padi(4 * k + 3)]);
+    for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
+      const uint32_t* w = wb + padi(4 * k);  // the 4 words never straddle a pad word
+      dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
     __syncthreads();
   }
 }
@@ -313,8 +314,8 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
     const uint4 v = __ldg(&s4[k]);
-    sm[padi(4 * k)] = v.x; sm[padi(4 * k + 1)] = v.y; sm[padi(4 * k + 2)] = v.z;
-    sm[padi(4 * k + 3)] = v.w;
+    uint32_t* w = sm + padi(4 * k);  // the 4 words never straddle a pad word
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
   }
   __syncthreads();
   ntt_inv_io<LOGN>(sm, c.mq[i], SmemLd{sm},
@@ -410,8 +411,8 @@ __global__ void __launch_bounds__(512) k_export(DevCtx c, const uint32_t* __rest
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
     const uint4 v = __ldg(&s4[k]);
-    sm[padi(4 * k)] = v.x; sm[padi(4 * k + 1)] = v.y; sm[padi(4 * k + 2)] = v.z;
-    sm[padi(4 * k + 3)] = v.w;
+    uint32_t* w = sm + padi(4 * k);  // the 4 words never straddle a pad word
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
   }
   __syncthreads();
   ntt_inv_io<LOGN>(sm, c.mq[l], SmemLd{sm}, [=](uint32_t k, uint32_t v) { dst[k] = v; });
