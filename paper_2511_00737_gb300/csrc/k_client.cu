@@ -363,6 +363,14 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
   uint32_t* o0 = out + ((size_t)(ct * 2 + 0) * c.L + l) * N;
   uint32_t* o1 = out + ((size_t)(ct * 2 + 1) * c.L + l) * N;
   const uint32_t* kl = gkj + ((size_t)l * L + l) * 4 * N;  // key parts of digit l
+  // every rank's transform buffer and key parts, resolved once
+  const uint32_t* xr[EPHDC_MAXL - 1];
+  const uint32_t* kr[EPHDC_MAXL - 1];
+#pragma unroll
+  for (uint32_t r = 0; r < EPHDC_MAXL - 1; r++) {
+    xr[r] = r < R ? cluster.map_shared_rank(x, r) : x;
+    kr[r] = gkj + ((size_t)(r < l ? r : r + 1) * L + l) * 4 * N;
+  }
   for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const uint32_t gp = galois_pos(j, gal, LOGN);
     uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[gp]);
@@ -373,12 +381,12 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
                                  __ldg(kl + 3 * N + j));
     uint32_t v[EPHDC_MAXL - 1];
     uint4 kv[EPHDC_MAXL - 1];
+    const uint32_t pj = padi(j);
 #pragma unroll
     for (uint32_t r = 0; r < EPHDC_MAXL - 1; r++) {
       if (r < R) {
-        const uint32_t d = r < l ? r : r + 1;
-        v[r] = cluster.map_shared_rank(x, r)[padi(j)];
-        const uint32_t* k = gkj + ((size_t)d * L + l) * 4 * N + j;
+        v[r] = xr[r][pj];
+        const uint32_t* k = kr[r] + j;
         kv[r] = make_uint4(__ldg(k), __ldg(k + N), __ldg(k + 2 * N), __ldg(k + 3 * N));
       }
     }
