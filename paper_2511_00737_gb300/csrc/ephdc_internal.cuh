@@ -44,7 +44,10 @@ struct DevCtx {
   const uint32_t* pos2slot;  // device NTT position j -> slot index rho*(n/2) + col
   const uint32_t* slot2pos;  // slot index -> device NTT position
   const uint32_t* galois;    // galois[j] = 3^(W*2^j) mod 2n, j < logr
-  const uint32_t* scatter;   // [(qidx * r + ch) * k_in + jin] -> device position
+  const uint32_t* scatter;   // [(qidx * r + ch) * k_in + jin] -> padded index of the
+                             // device position (padi of it, for the slot buffer)
+  const uint32_t* hslot;     // [b] = (int8 b mod t) * n^-1 mod t: the packed slot value,
+                             // scaled for an inverse transform without the n^-1 step
   uint32_t pack_rows;        // r when query rows pack by vector loads, else 0
   // context scratch used by kernels: fp16 copies of the HDC operands, status word
   uint16_t* xh;              // [max_batch][F] fp16 features
@@ -330,7 +333,9 @@ struct PaddedAccess<F, decltype((void)F::kPadded)> {
 };
 
 // FINAL: forward -> reduce outputs to [0, p); inverse -> multiply by n^-1, reduce
-template <int LOGN, int K, int LOGM0, bool FWD, bool FINAL, class LD, class ST>
+// NSCALE = false: the inverse's final pass only reduces (its input was scaled by n^-1)
+template <int LOGN, int K, int LOGM0, bool FWD, bool FINAL, class LD, class ST,
+          bool NSCALE = true>
 __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP& m, LD ld, ST st) {
   constexpr int LOGS = LOGN - LOGM0 - K;
   constexpr uint32_t S = 1u << LOGS;
@@ -393,9 +398,11 @@ __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP&
         if (FWD) {
           const uint32_t v = min(x[e], x[e] - two_p);
           x[e] = min(v, v - p);
-        } else {
+        } else if (NSCALE) {
           const uint32_t v = mulshoup(x[e], m.ninv, m.ninv_sh, p);
           x[e] = min(v, v - p);
+        } else {
+          x[e] = min(x[e], x[e] - p);
         }
       }
     }
@@ -428,22 +435,23 @@ __device__ __forceinline__ void fwd_passes(uint32_t* s, const ModP& m, LD ld, ST
     fwd_passes<LOGN, I + 1, LD, ST, V>(s, m, ld, st);
   }
 }
-template <int LOGN, int I, class LD, class ST, int V = 0>
+template <int LOGN, int I, class LD, class ST, int V = 0, bool NSCALE = true>
 __device__ __forceinline__ void inv_passes(uint32_t* s, const ModP& m, LD ld, ST st) {
   using Pl = NttPlan<LOGN, V>;
   if constexpr (I >= 0) {
     constexpr bool first = I == Pl::NP - 1, last = I == 0;
     if constexpr (first && last) {
-      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true>(m.itw, m, ld, st);
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true, LD, ST, NSCALE>(m.itw, m, ld, st);
     } else if constexpr (first) {
       pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, ld, SmemSt{s});
     } else if constexpr (last) {
-      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true>(m.itw, m, SmemLd{s}, st);
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true, SmemLd, ST, NSCALE>(m.itw, m, SmemLd{s},
+                                                                             st);
     } else {
       pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, SmemLd{s}, SmemSt{s});
     }
     __syncthreads();
-    inv_passes<LOGN, I - 1, LD, ST, V>(s, m, ld, st);
+    inv_passes<LOGN, I - 1, LD, ST, V, NSCALE>(s, m, ld, st);
   }
 }
 // Forward NTT: `ld(i)` supplies natural-order input i (values in [0, 4p)) to the first
@@ -455,18 +463,18 @@ __device__ __forceinline__ void ntt_fwd_io(uint32_t* s, const ModP& m, LD ld, ST
 }
 // Inverse NTT: device-order input (values in [0, 2p)) in, natural-order output in
 // [0, p) out.  Ends with a barrier.
-template <int LOGN, class LD, class ST, int V = 0>
+template <int LOGN, class LD, class ST, int V = 0, bool NSCALE = true>
 __device__ __forceinline__ void ntt_inv_io(uint32_t* s, const ModP& m, LD ld, ST st) {
-  inv_passes<LOGN, NttPlan<LOGN, V>::NP - 1, LD, ST, V>(s, m, ld, st);
+  inv_passes<LOGN, NttPlan<LOGN, V>::NP - 1, LD, ST, V, NSCALE>(s, m, ld, st);
 }
 // in-place variants on the padded shared buffer
 template <int LOGN, int V = 0>
 __device__ __forceinline__ void ntt_fwd_t(uint32_t* s, const ModP& m) {
   ntt_fwd_io<LOGN, SmemLd, SmemSt, V>(s, m, SmemLd{s}, SmemSt{s});
 }
-template <int LOGN, int V = 0>
+template <int LOGN, int V = 0, bool NSCALE = true>
 __device__ __forceinline__ void ntt_inv_t(uint32_t* s, const ModP& m) {
-  ntt_inv_io<LOGN, SmemLd, SmemSt, V>(s, m, SmemLd{s}, SmemSt{s});
+  ntt_inv_io<LOGN, SmemLd, SmemSt, V, NSCALE>(s, m, SmemLd{s}, SmemSt{s});
 }
 
 // dispatch a kernel template on log2(n) (n = 1024 .. 16384)
@@ -556,7 +564,9 @@ __device__ __forceinline__ void fill_gauss(const DevCtx& c, uint64_t seed, uint3
 // zeroed padded buffer mb (Sec. 3, SIMD form): query beta = g*cap + qidx (qidx =
 // rho*cap_row + qq) and dimension d = i*r + ch land in slot (rho, ch*W +
 // jin*cap_row + qq) for every jin < k_in.  Each value goes to its k_in device
-// positions through the context's scatter table.  No barrier.
+// positions through the context's scatter table (padded indices).  The value written
+// is h * n^-1 mod t (table hslot), so the inverse transform that follows skips its
+// n^-1 step (ntt_inv_t<..., false>).  No barrier.
 //
 // Rows path (c.pack_rows = r, with (r, k_in) one of (8, 1), (16, 1), (4, 2): D a
 // multiple of r, H aligned to r bytes): a thread takes whole query rows, the row's r
@@ -603,12 +613,12 @@ __device__ __forceinline__ void pack_query_rows(const DevCtx& c, const int8_t* _
       if (q0 + u * blockDim.x >= qlim) continue;
 #pragma unroll
       for (int e = 0; e < R; e++) {
-        const int h = (int)(int8_t)(row_word(hv[u], e >> 2) >> (8 * (e & 3)));
-        const uint32_t v = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
+        const uint32_t b = (row_word(hv[u], e >> 2) >> (8 * (e & 3))) & 0xFFu;
+        const uint32_t v = __ldg(&c.hslot[b]);
 #pragma unroll
         for (int j = 0; j < KIN; j++) {
           const int x = e * KIN + j;
-          mb[padi(row_word(sc[u][x >> 2], x & 3))] = v;
+          mb[row_word(sc[u][x >> 2], x & 3)] = v;
         }
       }
     }
@@ -632,10 +642,9 @@ __device__ __forceinline__ void pack_query_slots(const DevCtx& c, const int8_t* 
   for (uint32_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
     const uint32_t qidx = idx >> logr, ch = idx & (r - 1);
     if (ch >= dlim) continue;
-    const int h = Hg[(size_t)qidx * D + ch];
-    const uint32_t v = h < 0 ? (uint32_t)(h + (int)c.t) : (uint32_t)h;
+    const uint32_t v = __ldg(&c.hslot[(uint8_t)Hg[(size_t)qidx * D + ch]]);
     const uint32_t* sc = c.scatter + (size_t)idx * kin;
-    for (uint32_t jin = 0; jin < kin; jin++) mb[padi(__ldg(&sc[jin]))] = v;
+    for (uint32_t jin = 0; jin < kin; jin++) mb[__ldg(&sc[jin])] = v;
   }
 }
 

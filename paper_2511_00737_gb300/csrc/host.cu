@@ -275,7 +275,8 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
   // tables: twiddles for L primes + t (2 x n uint2 each), slot maps, Galois elements
   const int nm = p->L + 1;
   size_t tw_bytes = (size_t)nm * 4 * n * sizeof(uint2);  // tw, itw, twl, itwl
-  size_t map_bytes = 3 * (size_t)n * sizeof(uint32_t);  // slot2pos, pos2slot, scatter
+  // slot2pos, pos2slot, scatter, and the 256 scaled slot values
+  size_t map_bytes = (3 * (size_t)n + 256) * sizeof(uint32_t);
   size_t gal_bytes = 64 * sizeof(uint32_t);
   size_t total = align256(tw_bytes) + align256(map_bytes) + align256(gal_bytes);
   std::vector<uint8_t> host(total, 0);
@@ -343,12 +344,20 @@ ephdc_status ephdc_ctx_create(const ephdc_params* p, ephdc_ctx** out) {
       for (uint32_t jin = 0; jin < d.k_in; jin++) {
         const uint32_t rho = qidx / d.cap_row, qq = qidx % d.cap_row;
         const uint32_t sidx = rho * (n / 2) + ch * d.W + jin * d.cap_row + qq;
-        sct[(qidx * d.r + ch) * d.k_in + jin] = s2p[sidx];
+        sct[(qidx * d.r + ch) * d.k_in + jin] = s2p[sidx] + (s2p[sidx] >> 5);  // padded
       }
+  // packed slot value of a hypervector byte b: (int8 b mod t) n^-1 mod t
+  uint32_t* hsl = hmap + 3 * n;
+  for (uint32_t b = 0; b < 256; b++) {
+    const int32_t h = (int8_t)(uint8_t)b;
+    const uint64_t v = h < 0 ? (uint64_t)(h + (int64_t)t) : (uint64_t)h;
+    hsl[b] = (uint32_t)(v * d.mt.ninv % t);
+  }
   for (uint32_t j = 0; j < d.logr; j++) hgal[j] = pw(3, (uint64_t)d.W << j, 2 * n);
   d.slot2pos = (const uint32_t*)((uint8_t*)c->tables + align256(tw_bytes));
   d.pos2slot = d.slot2pos + n;
   d.scatter = d.slot2pos + 2 * n;
+  d.hslot = d.slot2pos + 3 * n;
   // whole query rows of r bytes fit one vector load when every row chunk is full
   d.pack_rows = (((d.k_in == 1 && (d.r == 8 || d.r == 16)) || (d.k_in == 2 && d.r == 4)) &&
                  d.D % d.r == 0) ? d.r : 0;

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 2)
   __syncthreads();
   pack_query_slots(c, H, B, g, i, mb);
   __syncthreads();
-  ntt_inv_t<LOGN, V>(mb, c.mt);  // slots -> m in [0, t)
+  ntt_inv_t<LOGN, V, false>(mb, c.mt);  // slots (scaled by n^-1) -> m in [0, t)
   for (uint32_t l = 0; l < c.L; l++) {
     const ModP m = c.mq[l];
     const uint32_t p = m.p;
