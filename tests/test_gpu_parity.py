@@ -5,6 +5,8 @@ and every output ciphertext in the coefficient domain, quantised hypervectors,
 plaintext polynomials, and decrypted scores, which must also equal the clear
 integer dot products mod t.  Calls go through the C ABI (via the ctypes binding).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -12,6 +14,8 @@ import torch
 import oracle as O
 from paper_2511_00737_gb300 import ephdc as E
 from paper_2511_00737_gb300 import workload as WL
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 pytestmark = pytest.mark.gpu
 
@@ -241,8 +245,9 @@ def test_face1024_full_size_bit_exact():
 def test_dense65536_full_size_sampled():
     """65536 queries, F=1024, D=16384, 8-bit HVs, 16 classes, n=16384, 6 primes, layout
     k_in=1 r=16 (64 groups, 4 rotations): sampled hypervector rows against the oracle's
-    projection and every sampled query's 16 decrypted scores against the clear dot
-    products mod t."""
+    projection, every sampled query's 16 decrypted scores against the clear dot
+    products mod t, and the score ciphertexts of groups 0 and 63 bit for bit against
+    the oracle's (by digest)."""
     w = WL.config("dense65536")
     ctx = E.Context.for_workload(w)
     X = WL.features(w.seed, w.B, w.F)
@@ -260,6 +265,17 @@ def test_dense65536_full_size_sampled():
     Ho = O.hdc_encode(X[rows], Wt, w.shift, w.bits)
     assert np.array_equal(H.cpu().numpy()[rows], Ho)
     assert np.array_equal(scores[rows], O.clear_scores(Ho, cls))
+    # groups 0 and 63 bit for bit: the digests of the oracle's score ciphertexts for
+    # those groups (tests/golden/make_dense65536_digests.py, oracle only)
+    import hashlib
+    words = _u32(out).reshape(-1, ctx.Kp, 2, w.L, w.n)
+    with open(os.path.join(GOLDEN, "dense65536_group_digests.txt")) as f:
+        digests = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(digests) == 2
+    for g, first, count, digest in digests:
+        assert int(first) == int(g) * ctx.cap and int(count) == ctx.cap
+        got = np.ascontiguousarray(words[int(g)], dtype="<u4")
+        assert hashlib.sha256(got.tobytes()).hexdigest() == digest, g
     ctx.close()
 
 
