@@ -1,5 +1,7 @@
 """Batching of many clients' uneven batches: packing, the tiled multi-group
 multiply-accumulate, CUDA-graph replay and the autotuner, against the oracle."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -126,8 +128,9 @@ def test_autotuner_picks_a_schedule_and_results_do_not_change(tmp_path, monkeypa
 @pytest.mark.slow
 def test_clients64_full_size_sampled():
     """64 clients, log-uniform batch sizes (sum ~ 31.5K), F=768, D=10000, 4-bit HVs,
-    7 classes, n=8192, 4 primes: sampled queries' hypervectors and decrypted scores
-    against the oracle's projection and the clear dot products."""
+    7 classes, n=8192, 4 primes: sampled queries' decrypted scores against the clear
+    dot products, and the score ciphertexts of three groups (one partial) bit for bit
+    against the oracle's (by digest)."""
     w = WL.config("clients64")
     ctx = E.Context.for_workload(w)
     dev = torch.device("cuda")
@@ -144,6 +147,21 @@ def test_clients64_full_size_sampled():
     rows = np.unique(np.concatenate([rng.integers(0, w.B, 256), [0, w.B - 1]]))
     H = O.hdc_encode(Xcat[rows], Wt, w.shift, w.bits)
     assert np.array_equal(scores[rows], O.clear_scores(H, cls))
+    # groups 0, 15 and the partial group 31 bit for bit: digests of the oracle's score
+    # ciphertexts on those rows of the concatenated batch
+    # (tests/golden/make_clients64_digests.py, oracle only)
+    import hashlib
+    words = _u32(out).reshape(-1, ctx.Kp, 2, w.L, w.n)
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                          "clients64_group_digests.txt")
+    with open(golden) as f:
+        digests = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(digests) == 3
+    for g, first, count, digest in digests:
+        assert int(first) == int(g) * ctx.cap
+        assert int(count) == min(ctx.cap, w.B - int(first))
+        got = np.ascontiguousarray(words[int(g)], dtype="<u4")
+        assert hashlib.sha256(got.tobytes()).hexdigest() == digest, g
     ctx.close()
 
 
