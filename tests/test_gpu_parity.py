@@ -227,10 +227,12 @@ def test_errors_are_reported_not_faulted(small):
 
 # ---------------------------------------------------------------- full size
 @pytest.mark.slow
-def test_face1024_full_size_bit_exact():
-    """1024 queries, F=608, D=10000, 8-bit HVs, 2 classes, n=8192, 4 primes: every score
-    ciphertext bit-exact, scores equal to the clear dot products mod t."""
-    c = Case(WL.config("face1024")).oracle_all().gpu_all()
+@pytest.mark.parametrize("name", ["face1024", "face1024_a"])
+def test_face1024_full_size_bit_exact(name):
+    """1024 queries, F=608, D=10000, 8-bit HVs, 2 classes, n=8192, 4 primes, in layout B
+    (k_in = 1, r = 8) and the paper's layout A (k_in = 2, r = 4): every score ciphertext
+    bit-exact, scores equal to the clear dot products mod t."""
+    c = Case(WL.config(name)).oracle_all().gpu_all()
     assert np.array_equal(c.g_H.cpu().numpy(), c.H)
     assert np.array_equal(_u32(c.g_out).reshape(c.out.shape), c.out)
     scores = _u32(c.ctx.decrypt_scores(c.g_sk, c.g_out, c.B))
