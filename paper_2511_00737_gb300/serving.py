@@ -190,7 +190,7 @@ class Server:
                         return True
         return False
 
-    # ------------------------------------------------------------------ driver
+    # ------------------------------------------------------------------ request loop
     def run(self, arrivals, make_X, time_scale=1.0):
         """Replays an arrival schedule in real time (arrival times in seconds,
         multiplied by time_scale) and serves it to completion."""
