@@ -45,7 +45,7 @@ def parse():
                     help="skip the client-runtime comparison with the server-side variant")
     ap.add_argument("--cpu-budget-s", type=float, default=20.0)
     ap.add_argument("--serve-requests", type=int, default=20000)
-    ap.add_argument("--streams", type=int, default=3,
+    ap.add_argument("--streams", type=int, default=4,
                     help="streams (contexts) that consecutive batches alternate over")
     ap.add_argument("--mac-mode", type=int, default=-1,
                     help="force the multiply-accumulate schedule (profiling)")
