@@ -366,3 +366,45 @@ def test_launch_count_matches_profiler(name):
                     "(%d records, e.g. %s)" % (len(raw), raw[:3]))
     assert claimed == len(names), sorted(set(names))
     ctx.close()
+
+
+def test_launch_count_of_packed_requests_matches_profiler():
+    """The same check for many clients' batches packed into one call (70 requests: two
+    gathers of up to 64 requests each)."""
+    w = WL.config("small")
+    sizes = [1 + (7 * i) % 13 for i in range(70)]
+    ctx = E.Context(w.n, w.L, w.k, w.k_in, w.r, w.D, w.F, w.bits, w.shift, sum(sizes) + 64)
+    Wt = _dev(WL.projection(w.seed, w.D, w.F))
+    Xs = [_dev(WL.features(w.seed, b, w.F, batch=i)) for i, b in enumerate(sizes)]
+    sk, gk = ctx.keygen(w.seed)
+    model = ctx.encrypt_model(_dev(WL.classes(w.seed, w.k, w.D)), sk, w.seed)
+    ctx.infer_multi(Xs, Wt, model, gk)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read()
+    from torch.profiler import ProfilerActivity, profile
+    with profile(activities=[ProfilerActivity.CUDA]):
+        torch.zeros(1, device="cuda").add_(1)
+        torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        ctx.infer_multi(Xs, Wt, model, gk)
+        torch.cuda.synchronize()
+    _, _, claimed = ctx.profile_read()
+    ctx.profile(False)
+    raw = []
+    try:
+        for e in prof.profiler.kineto_results.events():
+            raw.append((e.name(), str(e.device_type())))
+    except AttributeError:
+        raw = [(e.name, str(e.device_type)) for e in prof.events()]
+
+    def ours(n):
+        for pre in ("void ", "(anonymous namespace)::", "<unnamed>::", "ephdc::"):
+            n = n.replace(pre, "")
+        return n.startswith("k_")
+    names = [n for n, d in raw if "CUDA" in d and ours(n)]
+    if not names:
+        pytest.skip("the CUDA activity trace recorded none of this library's kernels")
+    assert sum("gather_widen" in n for n in names) == 2
+    assert claimed == len(names), sorted(set(names))
+    ctx.close()
