@@ -32,7 +32,6 @@ struct CentredLift {
     const uint32_t v = s[pi];
     return v <= thalf ? v : v + p_minus_t;
   }
-  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return at(padi(i)); }
 };
 
 // One CTA per plaintext (g, i).  The query slots are packed (pack_query_slots), the
