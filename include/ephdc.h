@@ -164,15 +164,19 @@ ephdc_status bfv_ptct_similarity(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t
  *    until the process exits.  The context must still be created beforehand (that
  *    call allocates the context's tables).
  *  - The first call on a device looks up the array's device address (with that
- *    device current); make that first call before any stream capture.
+ *    device current) and keeps it for the life of the process; make that first call
+ *    before any stream capture, and do not use this entry point on a device after a
+ *    cudaDeviceReset of it (the module, and with it the array, is loaded anew).
  *  - All calls share the one array, and it keeps the last call's contents (nothing
  *    in it needs to start at zero).  Calls whose work overlaps on the GPU -- on
  *    different streams, or from different contexts on the same device -- race on
  *    it: serialise them.
- *  - A batch whose score accumulators need more than the array (2*G*(k/k_in) ciphertexts
- *    plus one split of partial sums, G = ceil(B / cap)) is rejected with
- *    EPHDC_EINVAL before anything is enqueued.  With n = 8192 and L = 4 that is
- *    up to 9 score ciphertexts (G * k/k_in <= 9).
+ *  - A batch is rejected with EPHDC_EINVAL before anything is enqueued when its
+ *    scratch exceeds the array.  With C = G * (k/k_in) score ciphertexts of 2*L*n
+ *    words each (G = ceil(B / cap)), the scratch is two accumulator sets (2 C
+ *    ciphertexts), the key-switch digits (C * L * n words, half a set) and at least
+ *    one split of partial sums (C ciphertexts): 28 * C * L * n bytes.  With n = 8192
+ *    and L = 4 that allows C <= 9.
  * Arguments as for bfv_ptct_similarity. */
 #define EPHDC_STATIC_SCRATCH_BYTES (8u << 20)
 ephdc_status bfv_ptct_similarity_noalloc(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t B,
@@ -311,6 +315,17 @@ ephdc_status ephdc_ntt_natural(ephdc_ctx* ctx, uint32_t limb, uint32_t* poly_dev
  * This call waits for all work on the device and returns EPHDC_ETIMEOUT (clearing
  * the word) if any wait gave up since the last call, else EPHDC_OK. */
 ephdc_status ephdc_device_status(ephdc_ctx* ctx);
+
+/* Self-check of the bounded waits above (failure detection): enqueues on `stream`
+ * one single-thread kernel that initialises an mbarrier nothing ever arrives on and
+ * waits for it through the same bounded-wait routine as the tensor-core pipelines,
+ * giving up after limit_cycles SM clock cycles (1 .. 2^31; 10^5 is about 50 us).
+ * No copy or MMA is in flight while it waits.  The next ephdc_device_status then
+ * returns EPHDC_ETIMEOUT with code EPHDC_SELFCHECK_WAIT_CODE in its message, and the
+ * context stays usable.  The paper has no counterpart.  EPHDC_EINVAL for a limit
+ * out of range. */
+#define EPHDC_SELFCHECK_WAIT_CODE 99u
+ephdc_status ephdc_wait_selfcheck(ephdc_ctx* ctx, int64_t limit_cycles, void* stream);
 
 /* ---------------------------------------------------------------- measurement */
 /* Stages of the client path, for per-stage device timing. */

@@ -654,6 +654,8 @@ struct ephdc_ctx_impl;  // defined in host.cu
 // launch helpers implemented in the kernel translation units
 namespace ephdc {
 // X == NULL: the fp16 features are already in c.xh (see launch_gather_widen)
+cudaError_t launch_wait_selfcheck(const DevCtx& c, long long limit_cycles, uint32_t code,
+                                  cudaStream_t st);
 cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt, int B,
                               int8_t* H, cudaStream_t st);
 // rows of up to 64 requests, packed back to back into c.xh (fp16)

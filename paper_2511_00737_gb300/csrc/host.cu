@@ -1008,6 +1008,16 @@ ephdc_status ephdc_device_status(ephdc_ctx* c) {
   return EPHDC_OK;
 }
 
+ephdc_status ephdc_wait_selfcheck(ephdc_ctx* c, int64_t limit_cycles, void* stream) {
+  CHECK_CTX(c);
+  if (limit_cycles < 1 || limit_cycles > (1ll << 31))
+    return fail(c, EPHDC_EINVAL, "limit_cycles must be in [1, 2^31]");
+  return launched(c, ephdc::launch_wait_selfcheck(c->dc, (long long)limit_cycles,
+                                                  EPHDC_SELFCHECK_WAIT_CODE,
+                                                  (cudaStream_t)stream),
+                  "wait_selfcheck");
+}
+
 ephdc_status ephdc_profile_enable(ephdc_ctx* c, int on) {
   CHECK_CTX(c);
   c->prof = on != 0;

@@ -58,13 +58,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: gives up after ~2^31 cycles (about a second) and records `code`
+// bounded wait: gives up after `limit` cycles (by default 2^31, about a second) and
+// records `code`
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t* status,
-                                          uint32_t code) {
+                                          uint32_t code, long long limit = 1ll << 31) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1ll << 31)) {
+    if (clock64() - t0 > limit) {
       atomicCAS(status, 0u, code);
       return false;
     }
@@ -452,9 +453,28 @@ cudaError_t tensor_map(CUtensorMap* m, const void* base, uint64_t inner, uint64_
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Self-check of the bounded waits: one thread initialises an mbarrier that nothing
+// will ever arrive on and waits for its first phase through the same helper as the
+// pipelines, with a short limit.  The wait gives up, records `code` in the status
+// word and the kernel returns; no copy or MMA is in flight.
+__global__ void k_wait_selfcheck(uint32_t* status, long long limit, uint32_t code) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  mbar_wait(b, 0, status, code, limit);
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(b) : "memory");
+}
+
 }  // namespace
 
 namespace ephdc {
+
+cudaError_t launch_wait_selfcheck(const DevCtx& c, long long limit_cycles, uint32_t code,
+                                  cudaStream_t st) {
+  k_wait_selfcheck<<<1, 1, 0, st>>>(c.status, limit_cycles, code);
+  return cudaGetLastError();
+}
 
 static unsigned widen_blocks(size_t n) {
   return (unsigned)((n + 255) / 256 < 2432 ? (n + 255) / 256 : 2432);

@@ -67,6 +67,7 @@ _SIGS = {
     "bfv_ptct_similarity_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP,
                                                     _VP]),
     "ephdc_device_status": (ctypes.c_int, [_VP]),
+    "ephdc_wait_selfcheck": (ctypes.c_int, [_VP, ctypes.c_int64, _VP]),
     "ephdc_infer_multi": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "ephdc_tune_set": (ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_int64]),
     "ephdc_tune_get": (ctypes.c_int64, [_VP, ctypes.c_char_p]),
@@ -409,6 +410,12 @@ class Context:
     def device_status(self):
         """Raise EphdcError(EPHDC_ETIMEOUT) if a bounded device wait gave up."""
         _check(self.ctx, lib().ephdc_device_status(self.ctx))
+
+    def wait_selfcheck(self, limit_cycles, stream=None):
+        """Enqueue a kernel whose bounded wait cannot succeed and gives up after
+        limit_cycles; the next device_status() raises EPHDC_ETIMEOUT."""
+        _check(self.ctx, lib().ephdc_wait_selfcheck(self.ctx, int(limit_cycles),
+                                                    _stream(stream)))
 
     def profile(self, on=True):
         _check(self.ctx, lib().ephdc_profile_enable(self.ctx, 1 if on else 0))
