@@ -1,10 +1,16 @@
 """Continuous-batching serving loop for client-side encrypted HDC inference.
 
 Requests (one client's batch of feature rows each) arrive over time.  The loop
-- admits an arriving request while its device bytes (its features plus its share
-  of the score ciphertexts) fit in a device-memory budget that excludes the
-  resident encrypted model and rotation keys; a request larger than the whole
-  budget is rejected, the others wait in arrival order until memory frees up;
+- admits an arriving request when its feature rows can be placed in the feature
+  arena: one device buffer of `budget_bytes`, allocated once beside the resident
+  encrypted model and rotation keys and carved first-fit into 256-byte-aligned
+  ranges.  On admission the request's features are copied into its range on an
+  upload stream (from host memory or from a device tensor, ordered after the
+  caller's current stream), and the range is freed when the request completes or is
+  cancelled.  A request larger than the whole arena, or than one step, is rejected;
+  the others wait in arrival order until a range frees up.  The score ciphertexts
+  live in the slots' output buffers, allocated once per slot (slots x max_groups
+  groups), so admission changes no other allocation;
 - whenever one of its pipeline slots is idle, packs the admitted requests (up to
   the slot's group capacity) into one step and launches it on the slot's stream;
   each slot has its own context scratch, CUDA stream and CUDA graphs, and all slots
@@ -24,7 +30,6 @@ device is interrupted.  The slots are injectable (`slot_factory`), so the admiss
 packing, cancellation and bookkeeping logic runs on the host with fake slots.
 """
 import collections
-import math
 import time
 
 import numpy as np
@@ -34,9 +39,60 @@ from . import batching as BT
 from . import ephdc as E
 
 
+ALIGN = 256
+
+
+def request_bytes(F, B):
+    """Arena bytes of a request of B feature rows of F int8 features."""
+    return -(-(B * F) // ALIGN) * ALIGN
+
+
+class FeatureArena:
+    """First-fit allocator of 256-byte-aligned ranges of one preallocated device
+    buffer (`device` None: the bookkeeping alone, for host tests)."""
+
+    def __init__(self, capacity, device=None):
+        self.capacity = int(capacity) // ALIGN * ALIGN
+        self.buf = (torch.empty(self.capacity, dtype=torch.int8, device=device)
+                    if device is not None and self.capacity else None)
+        self.free = [(0, self.capacity)] if self.capacity else []  # sorted, disjoint
+        self.used = 0
+        self.peak = 0
+
+    def alloc(self, nbytes):
+        """Offset of a free range of nbytes (a multiple of ALIGN), or None."""
+        for i, (off, size) in enumerate(self.free):
+            if size >= nbytes:
+                if size == nbytes:
+                    del self.free[i]
+                else:
+                    self.free[i] = (off + nbytes, size - nbytes)
+                self.used += nbytes
+                self.peak = max(self.peak, self.used)
+                return off
+        return None
+
+    def release(self, off, nbytes):
+        i = 0
+        while i < len(self.free) and self.free[i][0] < off:
+            i += 1
+        self.free.insert(i, (off, nbytes))
+        # merge with the following and the preceding free range where they touch
+        if i + 1 < len(self.free) and off + nbytes == self.free[i + 1][0]:
+            self.free[i] = (off, nbytes + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == off:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+        self.used -= nbytes
+
+    def view(self, off, B, F):
+        return self.buf[off:off + B * F].view(B, F)
+
+
 class Request:
     __slots__ = ("rid", "arrival", "X", "B", "admitted", "launched", "done", "step",
-                 "rows", "nbytes", "cancelled")
+                 "rows", "nbytes", "cancelled", "off", "ready")
 
     def __init__(self, rid, arrival, X):
         self.rid, self.arrival, self.X = rid, arrival, X
@@ -46,6 +102,8 @@ class Request:
         self.rows = None
         self.nbytes = 0
         self.cancelled = False
+        self.off = None     # the request's range in the feature arena once admitted
+        self.ready = None   # event recorded after its features reached the arena
 
 
 class Step:
@@ -70,9 +128,18 @@ class Slot:
             self.pipe.graph(G) if self.pipe.use_graphs else None
         torch.cuda.synchronize()
 
-    def submit(self, Xs):
-        """Launches one packed step on this slot's stream; returns (pinned host copy of
-        the score ciphertexts, completion event, PackedBatch)."""
+    def submit(self, Xs, ready=None):
+        """Launches one packed step on this slot's stream once the events in `ready`
+        (one per request: its features are in place; None entries are skipped) have
+        completed; without `ready` the step is ordered after the caller's current
+        stream.  Returns (pinned host copy of the score ciphertexts, completion event,
+        PackedBatch)."""
+        if ready is None:
+            self.stream.wait_stream(torch.cuda.current_stream())
+        else:
+            for ev in ready:
+                if ev is not None:
+                    self.stream.wait_event(ev)
         with torch.cuda.stream(self.stream):
             out, pb = self.pipe.launch(Xs, self.stream)
             host = torch.empty(out.shape, dtype=out.dtype, pin_memory=True)
@@ -82,7 +149,14 @@ class Slot:
         return host, ev, pb
 
 
+DEFAULT_ARENA = 1 << 30
+
+
 class Server:
+    """budget_bytes: size of the feature arena (default: 1 GiB, or the free device
+    memory less 4 GiB if that is smaller).  With `slot_factory` (host tests) the arena
+    keeps its bookkeeping only and requests keep their own X."""
+
     def __init__(self, w, Wt, model, gk, slots=2, max_groups=8, budget_bytes=None,
                  use_graphs=True, keep_outputs=False, slot_factory=None):
         self.w = w
@@ -92,11 +166,17 @@ class Server:
         make = slot_factory or (lambda i: Slot(w, Wt, model, gk, max_groups, use_graphs))
         self.slots = [make(i) for i in range(slots)]
         self.max_queries = max_groups * self.cap
-        if budget_bytes is None:
-            free, _ = torch.cuda.mem_get_info()
-            budget_bytes = max(0, free - (4 << 30))
-        self.budget = int(budget_bytes)
-        self.used = 0
+        device = None
+        if slot_factory is None:
+            device = self.slots[0].ctx.device
+            if budget_bytes is None:
+                free, _ = torch.cuda.mem_get_info(device)
+                budget_bytes = min(DEFAULT_ARENA, max(0, free - (4 << 30)))
+            self.upload = torch.cuda.Stream(device=device)
+        elif budget_bytes is None:
+            budget_bytes = DEFAULT_ARENA
+        self.arena = FeatureArena(budget_bytes, device)
+        self.waited = 0
         self.keep_outputs = keep_outputs
         self.pending = collections.deque()   # arrived, not admitted (memory)
         self.queue = collections.deque()     # admitted, not launched
@@ -105,9 +185,16 @@ class Server:
         self.rejected = []
         self.cancelled = []
 
+    @property
+    def budget(self):
+        return self.arena.capacity
+
+    @property
+    def used(self):
+        return self.arena.used
+
     def request_bytes(self, B):
-        # the request's features on the device plus its share of score ciphertexts
-        return B * self.w.F + math.ceil(B / self.cap) * self.Kp * self.ct_bytes
+        return request_bytes(self.w.F, B)
 
     def warm(self):
         for s in self.slots:
@@ -122,13 +209,48 @@ class Server:
             return
         self.pending.append(req)
         self._admit(now)
+        if self.pending and self.pending[-1] is req:
+            self.waited += 1   # no free range on arrival: it waits for memory
 
     def _admit(self, now):
-        while self.pending and self.used + self.pending[0].nbytes <= self.budget:
-            r = self.pending.popleft()
-            self.used += r.nbytes
-            r.admitted = now
+        placed = []
+        while self.pending:
+            r = self.pending[0]
+            off = self.arena.alloc(r.nbytes)
+            if off is None:
+                break
+            self.pending.popleft()
+            r.off, r.admitted = off, now
+            self._place(r)
+            placed.append(r)
             self.queue.append(r)
+        if placed and self.arena.buf is not None:
+            # one event after the copies of everything admitted together
+            ev = torch.cuda.Event()
+            ev.record(self.upload)
+            for r in placed:
+                r.ready = ev
+
+    def _place(self, r):
+        """Copies an admitted request's features into its arena range on the upload
+        stream, after the work already on the caller's current stream (which may be
+        producing them); the request then holds the arena view."""
+        if self.arena.buf is None:
+            return
+        src = r.X if isinstance(r.X, torch.Tensor) else torch.from_numpy(np.asarray(r.X))
+        dst = self.arena.view(r.off, r.B, self.w.F)
+        if src.is_cuda:
+            self.upload.wait_stream(torch.cuda.current_stream(src.device))
+        with torch.cuda.stream(self.upload):
+            dst.copy_(src, non_blocking=True)
+        if src.is_cuda:
+            src.record_stream(self.upload)   # the caller may free X once this returns
+        r.X = dst
+
+    def _free(self, r):
+        if r.off is not None:
+            self.arena.release(r.off, r.nbytes)
+            r.off = None
 
     def _launch(self, slot, now):
         take, total = [], 0
@@ -138,7 +260,11 @@ class Server:
             total += r.B
         if not take:
             return False
-        host, ev, pb = slot.submit([r.X for r in take])
+        if self.arena.buf is None:
+            host, ev, pb = slot.submit([r.X for r in take])
+        else:
+            ready = list({id(r.ready): r.ready for r in take}.values())
+            host, ev, pb = slot.submit([r.X for r in take], ready)
         st = Step(len(self.steps), take, pb, host, ev, slot)
         for i, r in enumerate(take):
             r.launched, r.step, r.rows = now, st.sid, pb.rows(i)
@@ -155,7 +281,9 @@ class Server:
                 t = time.perf_counter() if now is None else now
                 for r in st.reqs:
                     r.done = t
-                    self.used -= r.nbytes
+                    self._free(r)
+                    if self.arena.buf is not None:
+                        r.X = None
                     (self.cancelled if r.cancelled else self.completed).append(r)
                 if not self.keep_outputs:
                     st.host_out = None
@@ -177,7 +305,9 @@ class Server:
                     dq.remove(r)
                     r.cancelled, r.done = True, now
                     if admitted:
-                        self.used -= r.nbytes
+                        # no slot reads it; a later upload into the range is ordered
+                        # after this request's own copy on the upload stream
+                        self._free(r)
                     self.cancelled.append(r)
                     self._admit(now)
                     return True
@@ -220,4 +350,6 @@ class Server:
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "steps": len(self.steps),
-                "mean_queries_per_step": q / max(1, len(self.steps)), "wall_s": wall_s}
+                "mean_queries_per_step": q / max(1, len(self.steps)), "wall_s": wall_s,
+                "arena_bytes": self.arena.capacity, "arena_peak_bytes": self.arena.peak,
+                "waited_for_memory": self.waited}

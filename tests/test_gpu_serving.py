@@ -16,7 +16,8 @@ def _u32(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def _serve(budget=None, n_req=60, rate=4000.0, slots=2, use_graphs=True, sizes=None):
+def _serve(budget=None, n_req=60, rate=4000.0, slots=2, use_graphs=True, sizes=None,
+           source="device"):
     w = WL.Workload(name="t", n=1024, L=3, k=3, k_in=1, r=4, D=120, F=32, bits=8, B=0, seed=9)
     dev = torch.device("cuda")
     Wt = WL.projection(w.seed, w.D, w.F)
@@ -33,7 +34,18 @@ def _serve(budget=None, n_req=60, rate=4000.0, slots=2, use_graphs=True, sizes=N
     srv = SV.Server(w, torch.from_numpy(Wt).to(dev), model, gk, slots=slots, max_groups=3,
                     budget_bytes=budget, use_graphs=use_graphs, keep_outputs=True)
     srv.warm()
-    wall = srv.run(t, lambda rid: Xd[rid])
+
+    def make_X(rid):
+        if source == "host":           # numpy rows, copied in by the server
+            return Xs[rid]
+        if source == "device_late":    # written on the current stream after a delay
+            X = torch.empty_like(Xd[rid])
+            torch.cuda._sleep(200000)
+            X.copy_(Xd[rid])
+            return X                   # the caller keeps no reference
+        return Xd[rid]
+
+    wall = srv.run(t, make_X)
     return w, keyctx, sk, gk, model, Wt, cls, Xs, Xd, srv, srv.report(wall)
 
 
@@ -62,13 +74,27 @@ def test_serving_results_equal_clear_scores_and_alone():
             assert np.array_equal(_u32(ctx.decrypt_scores(sk, alone, r.B)), mixed[r.rows])
 
 
-def test_admission_bounded_by_memory_budget():
-    # a 40-query request needs ~73 KB (features + one group of 3 score ciphertexts):
-    # 160 KB admits two at a time; the 600-query request (3 groups) never fits
+def test_admission_bounded_by_the_feature_arena():
+    # the arena is a real 2816-byte device buffer (3000 rounded down to 256-byte
+    # units); a 40-query request takes 1280 bytes of it (40 rows x 32 features), so
+    # two are admitted at a time and the others wait; the 600-query request (19200
+    # bytes) never fits and is rejected
     sizes = [40] * 20 + [600] + [40] * 10
-    w, keyctx, sk, gk, model, Wt, cls, Xs, Xd, srv, rep = _serve(budget=160 * 1024, sizes=sizes)
+    w, keyctx, sk, gk, model, Wt, cls, Xs, Xd, srv, rep = _serve(budget=3000, sizes=sizes)
+    assert srv.arena.buf is not None and srv.arena.buf.numel() == 2816
     assert [r.B for r in srv.rejected] == [600]
     assert rep["completed"] == len(sizes) - 1
+    assert rep["waited_for_memory"] > 0 and rep["arena_peak_bytes"] <= 2816
     assert max(len(st.reqs) for st in srv.steps) <= 2
-    assert srv.used == 0
+    assert srv.used == 0 and srv.arena.free == [(0, 2816)]
+    _check_results(w, keyctx, sk, srv, Wt, cls, Xs)
+
+
+@pytest.mark.parametrize("source", ["host", "device_late"])
+def test_features_from_host_or_written_late_on_the_callers_stream(source):
+    # features handed over as numpy rows, or written on the caller's stream behind a
+    # delay and dropped by the caller at once: the upload into the arena is ordered
+    # after the caller's stream and keeps the tensor alive, so scores stay exact
+    w, keyctx, sk, gk, model, Wt, cls, Xs, Xd, srv, rep = _serve(n_req=30, source=source)
+    assert rep["completed"] == len(Xs) and rep["rejected"] == 0
     _check_results(w, keyctx, sk, srv, Wt, cls, Xs)

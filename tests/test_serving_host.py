@@ -57,9 +57,8 @@ def finish_all(srv, fakes, t):
 
 
 def test_admission_in_arrival_order_within_budget():
-    srv, fakes = server(budget=0)
-    one = srv.request_bytes(100)
-    srv.budget = 2 * one
+    one = SV.request_bytes(W.F, 100)
+    srv, fakes = server(budget=2 * one)
     for rid in range(4):
         srv.arrive(req(rid, 100), 0.0)
     assert [r.rid for r in srv.queue] == [0, 1] and [r.rid for r in srv.pending] == [2, 3]
@@ -80,15 +79,15 @@ def test_admission_in_arrival_order_within_budget():
 def test_requests_that_can_never_fit_are_rejected():
     srv, _ = server(budget=10 ** 9)
     srv.arrive(req(0, 2 * CAP + 1), 0.0)            # more than a step's 2 groups
-    srv.budget = srv.request_bytes(50) - 1
-    srv.arrive(req(1, 50), 0.0)                     # more than the whole budget
-    assert [r.rid for r in srv.rejected] == [0, 1] and srv.used == 0
-    assert srv.report(1.0)["rejected"] == 2
+    assert [r.rid for r in srv.rejected] == [0] and srv.used == 0
+    srv, _ = server(budget=SV.request_bytes(W.F, 50) - 1)
+    srv.arrive(req(1, 50), 0.0)                     # more than the whole arena
+    assert [r.rid for r in srv.rejected] == [1] and srv.used == 0
+    assert srv.report(1.0)["rejected"] == 1
 
 
 def test_cancel_waiting_queued_and_in_flight():
-    srv, fakes = server(budget=0, slots=1, max_groups=1)
-    srv.budget = 2 * srv.request_bytes(200)
+    srv, fakes = server(budget=2 * SV.request_bytes(W.F, 200), slots=1, max_groups=1)
     for rid, B in enumerate([200, 200, 200, 10]):
         srv.arrive(req(rid, B), 0.0)
     srv.poll(0.0)                      # request 0 in flight (a step holds one group)
@@ -122,3 +121,36 @@ def test_each_completed_request_owns_its_packed_rows():
             assert r.rows.start == end and r.rows.stop - r.rows.start == r.B
             end = r.rows.stop
         assert end <= 2 * CAP
+
+
+def test_feature_arena_first_fit_and_coalescing():
+    a = SV.FeatureArena(10 * SV.ALIGN)
+    x = a.alloc(3 * SV.ALIGN)
+    y = a.alloc(3 * SV.ALIGN)
+    z = a.alloc(3 * SV.ALIGN)
+    assert (x, y, z) == (0, 3 * SV.ALIGN, 6 * SV.ALIGN) and a.used == 9 * SV.ALIGN
+    assert a.alloc(2 * SV.ALIGN) is None            # one aligned unit left
+    a.release(y, 3 * SV.ALIGN)
+    assert a.alloc(4 * SV.ALIGN) is None            # 3 + 1 free units, not adjacent
+    a.release(z, 3 * SV.ALIGN)                      # merges with y's range and the tail
+    assert a.free == [(3 * SV.ALIGN, 7 * SV.ALIGN)]
+    assert a.alloc(7 * SV.ALIGN) == 3 * SV.ALIGN
+    a.release(x, 3 * SV.ALIGN)
+    a.release(3 * SV.ALIGN, 7 * SV.ALIGN)
+    assert a.free == [(0, 10 * SV.ALIGN)] and a.used == 0 and a.peak == 10 * SV.ALIGN
+
+
+def test_admission_waits_for_a_contiguous_range():
+    unit = SV.request_bytes(W.F, 8)                  # 256 bytes
+    srv, fakes = server(budget=4 * unit, slots=1, max_groups=1)
+    for rid, B in enumerate([8, 8, 8, 8]):
+        srv.arrive(req(rid, B), 0.0)
+    assert srv.used == 4 * unit and srv.waited == 0
+    srv.arrive(req(4, 16), 0.0)                       # needs two adjacent units
+    assert [r.rid for r in srv.pending] == [4] and srv.waited == 1
+    srv.poll(0.0)                                     # one step takes all four
+    assert fakes[0].steps == [[8, 8, 8, 8]]
+    while finish_all(srv, fakes, 0.1):
+        pass
+    assert sorted(r.rid for r in srv.completed) == [0, 1, 2, 3, 4] and srv.used == 0
+    assert srv.report(1.0)["waited_for_memory"] == 1
