@@ -60,6 +60,8 @@ def parse():
                     help="override the hypervector dimension D (profiling of smaller cases)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="time only the headline workload (not clients64, serve, dense65536)")
     return ap.parse_args()
 
 
@@ -202,6 +204,30 @@ def config_of(w, B, per_step=None):
                   "larger than the 129 MB L2", "parallelism": "replicas"}
 
 
+# ------------------------------------------------------------------ parity of the timed work
+DIGESTS = {"face1024": "face1024x16", "clients64": "clients64", "dense65536": "dense65536"}
+
+
+def digest_check(out, ctx, name):
+    """Compares query groups of the score ciphertexts in `out` (coefficient domain,
+    [G][k/k_in][2][L][n]) word for word with the SHA-256 digests of the oracle's
+    ciphertexts stored in tests/golden/<name>_group_digests.txt (written by the
+    committed script beside it, which runs only the oracle)."""
+    import hashlib
+    path = os.path.join(ROOT, "tests", "golden", name + "_group_digests.txt")
+    words = out.cpu().numpy().view(np.uint32).reshape(-1, ctx.Kp, 2, ctx.L, ctx.n)
+    groups, ok = [], True
+    for line in open(path):
+        if not line.strip() or line.startswith("#"):
+            continue
+        g, _, _, digest = line.split()
+        got = np.ascontiguousarray(words[int(g)], dtype="<u4")
+        ok = ok and hashlib.sha256(got.tobytes()).hexdigest() == digest
+        groups.append(int(g))
+    return {"checked": "score ciphertexts of groups %s vs oracle digests (%s)" % (
+        groups, os.path.basename(path)), "match": bool(ok)}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, w, B):
     import torch
@@ -340,6 +366,16 @@ def run_ours(args, w, B):
         return sm_, sc_, ln_
 
     stage_ms, stage_calls, launches = read_stages()
+    # the timed work's own output: the last timed step on stream 0 used feature set
+    # last % R; with the digests' inputs (set 0 of the rank-0 seed) check it
+    parity = None
+    can_check = (rank == 0 and not args.dim and not args.batch and w.name in DIGESTS and
+                 (multi or (w.name != "face1024" or (batch == 1024 and pack == 16))))
+    if can_check and not multi:
+        last = max(i for i in range(args.steps) if i % S == 0)
+        if last % R == 0:
+            parity = digest_check(outs[0], ctx, DIGESTS[w.name])
+            parity["step"] = "timed step %d (stream 0)" % last
     roof_pass = "the timed region"
     if not multi and S > 1:
         # overlapping batches stretch each kernel's event time: take the per-stage
@@ -366,6 +402,11 @@ def run_ours(args, w, B):
         stage_calls = {k: v * args.steps // ksteps_eager for k, v in stage_calls.items()}
         launches = launches * args.steps // ksteps_eager
         pipe.use_graphs = True
+        if can_check:
+            res, _ = pipe.run(Xd[0])   # the timed step's graph on feature set 0
+            torch.cuda.synchronize()
+            parity = digest_check(res, ctx, DIGESTS[w.name])
+            parity["step"] = "one graph-replayed step on feature set 0 after the timed region"
     for cx in all_ctx:
         cx.profile(False)
     value, ms_total = RP.job_throughput(B * args.steps, e0.elapsed_time(e1), world, device=dev)
@@ -437,7 +478,8 @@ def run_ours(args, w, B):
                 "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
                 "roofline": roof, "cpu_baseline": cpu,
                 "stages_ms_per_step": {k: v / max(1, args.steps) for k, v in stage_ms.items()},
-                "per_query_form": perq, "client_runtime_vs_server_side": clrt}
+                "per_query_form": perq, "client_runtime_vs_server_side": clrt,
+                "parity": parity}
         if not multi:
             line["config"]["streams"] = S
             line["config"]["batches_per_step"] = pack
@@ -448,11 +490,11 @@ def run_ours(args, w, B):
             line["config"]["clients"] = len(w.clients)
             line["config"]["mac_schedule"] = tuned
             line["config"]["cuda_graph"] = True
-        print(json.dumps(line), flush=True)
     for cx in ([ctx] if multi else ctxs):
         cx.close()
     if dist is not None:
         dist.destroy_process_group()
+    return line if rank == 0 else None
 
 
 def client_runtime(w, dev, B, reps=5):
@@ -643,8 +685,12 @@ def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
                 "peak": peak, "unit": "Tbutterfly/s", "frac": ach / peak,
                 "traffic": NCU_TRAFFIC.get((w.name, G, "encode_plain")),
                 "algorithmic_bytes": B * w.D + G * P * L * n * 4,
-                "peak_source": "derived: 152 SMs x 128 integer lanes x %.0f MHz / 8 instructions "
-                               "per lazy Shoup butterfly" % pk.get("sm_max_mhz", 2070.0),
+                "peak_source": "pipe model: the lazy Shoup butterfly is bound by the FMA-heavy "
+                               "pipe (its multiplies); %.2f butterflies per SM cycle with that "
+                               "pipe busy every cycle (ncu on the register-only butterfly loop: "
+                               "95.4%% FMA-heavy active, 51.3%% ALU) x 152 SMs x %.0f MHz" % (
+                                   BFLY_PER_SM_CYCLE, pk.get("sm_max_mhz", 2070.0)),
+                "peak_old_derivation": 152 * 4 * 32 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 8 / 1e12,
                 "measured_peak": pk["bfly_tps"], "frac_of_measured": ach / pk["bfly_tps"],
                 "measured_peak_source": "register-only lazy Shoup butterflies "
                                         "(ephdc_measure_int_peaks)",
@@ -661,12 +707,17 @@ def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
             "frac": None, "traffic": None, "ms_per_launch": t * 1000.0}
 
 
+# Butterflies per SM cycle of a lazy Shoup butterfly with the FMA-heavy pipe (which runs
+# its integer multiplies) busy every cycle.  From one ncu capture of the register-only
+# butterfly loop (k_bfly_peak, 4.08e10 butterflies, 2.59e7 SM cycles): that pipe 95.44%
+# active at 3.254 T butterflies/s, i.e. 4.08e10 / (0.9544 x 2.59e7 x 152) per SM cycle.
+# The ALU pipe was 51.3% active, so the FMA-heavy pipe binds.
+BFLY_PER_SM_CYCLE = 4.0803e10 / (0.9544 * 25898462.62 * 152)
+
+
 def alu_peak_tbfly(pk):
-    # 152 SMs x 4 SM sub-partitions x 32 lanes x clock, one 32-bit instruction per lane
-    # per cycle; a lazy Shoup butterfly issues 8 integer instructions (3 multiplies,
-    # 5 adds/selects), so the issue-limited rate is lanes x clock / 8
     mhz = pk.get("sm_max_mhz", 2070.0)
-    return 152 * 4 * 32 * mhz * 1e6 / 8 / 1e12
+    return 152 * mhz * 1e6 * BFLY_PER_SM_CYCLE / 1e12
 
 
 def alu_peak_tmac(pk):
@@ -699,10 +750,15 @@ def run_serve(args, w):
     offs = np.random.default_rng(seed).integers(0, pool_rows - 8192, len(sizes))
     make_X = lambda rid: pool[offs[rid]:offs[rid] + int(sizes[rid])]
     results = {}
+    clk = None
     for name, scale in (("poisson_2000_rps", 1.0), ("all_at_once", 0.0)):
         srv = SV.Server(w, Wt, model, gk, slots=2, max_groups=8)
         srv.warm()
+        clocks = ClockSampler(local)
+        clocks.start()
         wall = srv.run(t, make_X, time_scale=scale)
+        c = clocks.stop()
+        clk = clk or c
         results[name] = srv.report(wall)
         for s_ in srv.slots:
             s_.ctx.close()
@@ -715,15 +771,15 @@ def run_serve(args, w):
                 "n_gpus": world, "steps": live["steps"], "warmup": 0,
                 "ms_per_step": 1e3 * live["wall_s"] / max(1, live["steps"]),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "u32", "data": "synthetic",
+                "dtype": "u32", "data": "synthetic", "clocks": clk,
                 "config": {"workload": "serve: %d requests, Poisson 2000 req/s, lognormal "
                                        "batch (median 32, max 8192), F=%d, D=%d, k=%d, n=%d, "
                                        "L=%d, layout k_in=%d r=%d; 2 slots x 8 groups" % (
                                            len(sizes), w.F, w.D, w.k, w.n, w.L, w.k_in, w.r),
                            "offered_queries_per_s": offered},
                 "serving": results}
-        print(json.dumps(line), flush=True)
     keyctx.close()
+    return line if rank == 0 else None
 
 
 def main():
@@ -745,10 +801,47 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, w, B if B else 1024)
-    elif args.workload == "serve" and not args.batch:
-        run_serve(args, w)
+        return
+    if args.workload == "serve" and not args.batch:
+        line = run_serve(args, w)
     else:
-        run_ours(args, w, B)
+        line = run_ours(args, w, B)
+    _, _, world = dist_env()
+    if (line is not None and args.workload == "face1024" and not args.batch and not args.dim
+            and world == 1 and not args.no_legs):
+        line["legs"] = run_legs(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+# the other workloads of the metric's parameters (D = 10000, n = 8192) and the dense
+# one, each timed on its own after the headline (1 GPU only), with fewer steps
+LEG_KEYS = ("value", "unit", "steps", "warmup", "ms_per_step", "config", "clocks", "e2e",
+            "gpu_launches", "roofline", "stages_ms_per_step", "parity", "serving")
+
+
+def run_legs(args):
+    import copy
+    import torch
+    from paper_2511_00737_gb300 import workload as WL
+    out = {}
+    for name, steps in (("clients64", 50), ("serve", 0), ("dense65536", 5)):
+        a = copy.copy(args)
+        a.workload = name
+        a.steps = max(1, min(args.steps, steps))
+        a.warmup = 3
+        a.no_cpu_baseline = a.no_perquery = a.no_sr = True
+        a.pack, a.mac_mode, a.mac_tile, a.hdc_mode = 0, -1, -1, -1
+        w = WL.config(name)
+        t0 = time.perf_counter()
+        line = run_serve(a, w) if name == "serve" else run_ours(a, w, w.B)
+        rec = {k: line[k] for k in LEG_KEYS if k in line}
+        rec["wall_s"] = time.perf_counter() - t0
+        if name == "serve":
+            rec["steps"] = line["steps"]
+        out[name] = rec
+        torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":
