@@ -166,10 +166,11 @@ def test_clients64_full_size_sampled():
 
 
 @pytest.mark.parametrize("k,groups,D", [
-    (7, 11, 1200),   # 14 outputs: one M tile, N = 64; P = 300: two 256-windows, ragged K
-    (5, 40, 300),    # 10 outputs, 40 groups: two M tiles (64 groups per CTA), N = 64
-    (16, 9, 520),    # 32 outputs: N = 128, two coefficients per CTA
-    (16, 70, 64),    # 32 outputs, 70 groups: two group blocks of two M tiles
+    (7, 11, 1200),   # 14 outputs (rows past O zero); P = 300: two 256-windows, ragged chunk
+    (5, 40, 300),    # 10 outputs, 40 groups (columns past G zero)
+    (16, 9, 520),    # 32 outputs: all 32 rows of every digit block
+    (16, 70, 64),    # 32 outputs, 70 groups: two group blocks of 64
+    (2, 3, 2100),    # 4 outputs, P = 525: three windows, the last one partial
 ])
 def test_tensor_core_mac_equals_streaming(k, groups, D):
     """The exact byte-split tensor-core product gives the same accumulators (and so the
@@ -186,4 +187,41 @@ def test_tensor_core_mac_equals_streaming(k, groups, D):
     if groups <= 11:
         H = O.hdc_encode(np.concatenate(Xs), Wt, w.shift, w.bits)
         assert np.array_equal(_u32(ctx.decrypt_scores(sk, got, w.B)), O.clear_scores(H, cls))
+    ctx.close()
+
+
+@pytest.mark.parametrize("fill", ["max_negative_digits", "q_minus_1", "random"])
+def test_tensor_core_mac_exact_at_extreme_residues(fill):
+    """The signed-digit tensor-core product against the 64-bit CUDA-core one on
+    hand-made plaintexts and models: every residue q_l - 1, every residue with the
+    most negative balanced digits a residue below 2^30 can have (8355712: digits
+    -128, -128, -128, 1), or random residues; 32 outputs, 70 groups (two group blocks),
+    P = 300 (a full and a partial window)."""
+    w = WL.Workload(name="t", n=1024, L=3, k=16, k_in=1, r=4, D=1200, F=32, bits=8,
+                    B=70 * 256, seed=5)
+    ctx = E.Context.for_workload(w)
+    sk, gk = ctx.keygen(w.seed)
+    G, P, L, n = ctx.groups(w.B), ctx.P, w.L, w.n
+    assert G == 70 and P == 300
+    rng = np.random.default_rng(9)
+    q = np.array(ctx.q, dtype=np.uint64)
+
+    def make(shape):
+        if fill == "q_minus_1":
+            a = np.broadcast_to((q - 1).reshape(L, 1), shape[:-2] + (L, n))
+        elif fill == "max_negative_digits":
+            a = np.full(shape, 8355712, np.uint64)
+        else:
+            a = rng.integers(0, 1 << 62, size=shape, dtype=np.uint64) % q.reshape(L, 1)
+        return _dev(np.ascontiguousarray(a).astype(np.uint32).view(np.int32))
+
+    pt = make((G, P, L, n))
+    model = make((P, ctx.Kp, 2, L, n))
+    assert (-8421504 + 16777216) == 8355712  # -128 (1 + 2^8 + 2^16) + 2^24
+    ctx.tune_set("mac_mode", 1)
+    ref = ctx.ptct_similarity(pt, w.B, model, gk)
+    ctx.tune_set("mac_mode", 3)
+    got = ctx.ptct_similarity(pt, w.B, model, gk)
+    ctx.device_status()
+    assert torch.equal(got, ref)
     ctx.close()

@@ -278,6 +278,11 @@ def test_dense65536_full_size_sampled():
         assert int(first) == int(g) * ctx.cap and int(count) == ctx.cap
         got = np.ascontiguousarray(words[int(g)], dtype="<u4")
         assert hashlib.sha256(got.tobytes()).hexdigest() == digest, g
+    # the tensor-core and the tiled CUDA-core products give the same ciphertexts
+    for mode in (3, 2):
+        ctx.tune_set("mac_mode", mode)
+        assert torch.equal(ctx.infer(gX, gW, model, gk), out), mode
+    ctx.device_status()
     ctx.close()
 
 
