@@ -60,6 +60,9 @@ def parse():
                     help="override the hypervector dimension D (profiling of smaller cases)")
     ap.add_argument("--batch", type=int, default=0,
                     help="override the workload's batch size (profiling of smaller cases)")
+    ap.add_argument("--layout", type=int, default=-1,
+                    help="storage layout of plaintexts and model (0 standard, 1 "
+                         "coefficient-blocked); default: 1 for n >= 16384")
     ap.add_argument("--no-legs", action="store_true",
                     help="time only the headline workload (not clients64, serve, dense65536)")
     return ap.parse_args()
@@ -256,6 +259,10 @@ def run_ours(args, w, B):
         from paper_2511_00737_gb300 import batching as BT
     # packed multi-client steps replay whole groups, so reserve full groups
     ctx = E.Context.for_workload(w, max_batch=(-(-B // cap) * cap) if multi else B)
+    # storage layout of plaintexts and model: coefficient-blocked (read by the
+    # tensor-core product) for the dense shapes, unless forced
+    layout = args.layout if args.layout >= 0 else int(w.n >= 16384 and 2 * (w.k // w.k_in) <= 32)
+    ctx.tune_set("layout", layout)
     if args.mac_mode >= 0:
         ctx.tune_set("mac_mode", args.mac_mode)
     if args.hdc_mode >= 0:
@@ -304,6 +311,7 @@ def run_ours(args, w, B):
         S = max(1, args.streams)
         ctxs = [ctx] + [E.Context.for_workload(w, max_batch=B) for _ in range(S - 1)]
         for cx in ctxs[1:]:
+            cx.tune_set("layout", layout)  # the shared model's layout
             if tuned:
                 AT.apply(cx, tuned)
             if args.hdc_mode >= 0:
@@ -484,6 +492,7 @@ def run_ours(args, w, B):
             line["config"]["streams"] = S
             line["config"]["batches_per_step"] = pack
             line["config"]["batch"] = batch
+        line["config"]["storage_layout"] = "coefficient-blocked" if layout else "standard"
         if not multi and tuned:
             line["config"]["mac_schedule"] = tuned
         if multi:

@@ -282,8 +282,16 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * persistent 128 x 256 with a 4-stage ring);
  * "ntt_plan" 0/1/2
  * is the pass schedule of the encoding transforms (balanced, radix-32 passes first,
- * radix-32 passes last).  EPHDC_EINVAL for an unknown
- * knob or an invalid value.  ephdc_tune_get returns -1 for an unknown knob. */
+ * radix-32 passes last).  "layout" 0/1 is the device order of the NTT-domain
+ * plaintexts and model: 0 = [G][P][L][n] and [P][k/k_in][2][L][n]; 1 = blocked by 4
+ * coefficients, [L][n/4][G][P][4] and [L][n/4][P][2 k/k_in][4] (needs k/k_in <= 16),
+ * read by the tensor-core product with every tile's data contiguous.  Set "layout"
+ * before bfv_encrypt_model: a model is only valid for contexts with the layout it was
+ * encrypted under.  With layout 1 the multiply-accumulate always runs on the tensor
+ * cores ("mac_mode" 1 or 2 fails with EPHDC_EUNSUPPORTED), and the seeded model message,
+ * the server-side variant, the noise-growth trial and bfv_ptct_similarity_noalloc
+ * return EPHDC_EUNSUPPORTED.  EPHDC_EINVAL for an unknown knob or an invalid value.
+ * ephdc_tune_get returns -1 for an unknown knob. */
 ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);
 int64_t ephdc_tune_get(const ephdc_ctx* ctx, const char* knob);
 
@@ -297,8 +305,12 @@ ephdc_status ephdc_sk_to_host(ephdc_ctx* ctx, const void* sk_dev, int32_t* host)
 /* Galois keys to the host, uint32 [log2 r][L digits][2][L limbs][n] coefficient
  * domain.  Synchronous. */
 ephdc_status ephdc_gk_to_host_coeff(ephdc_ctx* ctx, const void* gk_dev, uint32_t* host);
+/* The encrypted model (either layout) to the host in the coefficient domain, uint32
+ * [P][k/k_in][2][L][n].  Synchronous; allocates temporary device memory. */
+ephdc_status ephdc_model_to_host_coeff(ephdc_ctx* ctx, const void* model_dev, uint32_t* host);
 /* Plaintexts from bfv_encode_plain to the host as the lifted plaintext polynomial
- * per limb, uint32 [count][L][n] in [0, q_l).  Synchronous. */
+ * per limb, uint32 [count][L][n] in [0, q_l); with layout 1, count must be a whole
+ * number of groups (G * P).  Synchronous. */
 ephdc_status ephdc_plain_to_host_coeff(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t count,
                                        uint32_t* host);
 

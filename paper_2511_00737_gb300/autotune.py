@@ -6,7 +6,8 @@ only the speed), applies the fastest and remembers it in a JSON cache keyed by
 GPU, ring degree, limbs, layout and G.  Candidates: the streaming kernel split
 over plaintext ranges (several split caps), and the tiled multi-group kernel with
 2 or 4 groups and 4, 7 or 8 outputs per warp, 8 to 64 groups per CTA and 4 to 15
-plaintexts per staged chunk, and the exact byte-split product on the tensor cores.
+plaintexts per staged chunk, and the exact signed-digit product on the tensor cores
+(the only candidate when the context stores plaintexts and model coefficient-blocked).
 """
 import json
 import os
@@ -19,7 +20,8 @@ CACHE = os.environ.get("EPHDC_TUNE_CACHE",
 
 def _key(ctx, G):
     name = torch.cuda.get_device_name(ctx.device).replace(" ", "_")
-    return "%s|n%d|L%d|k%d|kin%d|r%d|G%d" % (name, ctx.n, ctx.L, ctx.k, ctx.k_in, ctx.r, G)
+    return "%s|n%d|L%d|k%d|kin%d|r%d|G%d|lay%d" % (name, ctx.n, ctx.L, ctx.k, ctx.k_in, ctx.r, G,
+                                                  ctx.tune_get("layout"))
 
 
 def _load():
@@ -39,6 +41,8 @@ def _save(d):
 
 def candidates(ctx, G):
     O = 2 * ctx.Kp
+    if ctx.tune_get("layout") == 1:
+        return [{"mac_mode": 3}]   # the blocked layout is read by the tensor cores only
     out = [{"mac_mode": 1, "mac_splits": s} for s in (0, 8, 16, 32)]
     if G >= 2 and O <= 32:
         out.append({"mac_mode": 3})

@@ -64,7 +64,22 @@ struct DevCtx {
   // scale_w[l] = the centred lift of (2^s)^-1 mod t; scale_g = g (0 = off)
   uint32_t scale_g;
   uint32_t scale_w[EPHDC_MAXL];
+  // NTT-domain storage of plaintexts and model: 0 = plaintexts [G][P][L][n] and model
+  // [P][O][L][n] (O = 2 k/k_in outputs o = j' * 2 + poly); 1 = coefficient-blocked,
+  // [L][n/4][G][P][4] and [L][n/4][P][O][4], so that the 4 coefficients of a block of
+  // every (group, plaintext) and (plaintext, output) pair are 16 contiguous bytes and a
+  // block's pairs are contiguous (read by the tensor-core multiply-accumulate)
+  uint32_t layout;
 };
+
+// word index of coefficient k of limb l of pair (a, b) in the blocked layout
+// [L][n/4][A][B][4] (plaintexts: a = group, b = plaintext; model: a = plaintext,
+// b = output)
+__host__ __device__ __forceinline__ size_t blk_index(uint32_t n, uint32_t A, uint32_t B,
+                                                      uint32_t a, uint32_t b, uint32_t l,
+                                                      uint32_t k) {
+  return ((((size_t)l * (n >> 2) + (k >> 2)) * A + a) * B + b) * 4 + (k & 3);
+}
 
 
 // ------------------------------------------------------------------ arithmetic
@@ -717,6 +732,8 @@ cudaError_t launch_decrypt_scores(const DevCtx& c, const uint32_t* sk, const uin
                                   int B, uint32_t* xbuf, uint32_t* scores, cudaStream_t st);
 cudaError_t launch_ntt_natural(const DevCtx& c, uint32_t limb, uint32_t* poly, int count,
                                int inverse, cudaStream_t st);
+cudaError_t launch_unblock(const DevCtx& c, const uint32_t* src, uint32_t* dst, uint32_t A,
+                           uint32_t B, cudaStream_t st);
 cudaError_t launch_to_coeff(const DevCtx& c, const uint32_t* in, uint32_t* out, int count,
                             int limbs_per_item, int in_stride_words, int limb_stride_words,
                             int limb0_is_digit_major, cudaStream_t st);

@@ -572,11 +572,14 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
   cudaError_t e;
   {
     const bool tc_ok = 2 * d.Kp <= 32 && d.P < 16384;
-    const bool tc = tc_ok && (c->mac_mode == 3 ||
+    // the blocked layout is read by the tensor-core product only
+    if (d.layout && (c->mac_mode == 1 || c->mac_mode == 2))
+      return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs mac_mode 0 or 3");
+    const bool tc = tc_ok && (c->mac_mode == 3 || d.layout ||
                               (c->mac_mode == 0 && G >= c->mac_tc_min_groups));
     const bool tiled = !tc && (c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups));
     StageTimer tm(c, EPHDC_STAGE_MAC, st, tc || tiled ? 1 : (2 * d.Kp + 3) / 4 + 1);
-    if (c->mac_mode == 3 && !tc_ok) {
+    if ((c->mac_mode == 3 || d.layout) && !tc_ok) {
       e = cudaErrorNotSupported;
     } else if (tc) {
       e = ephdc::launch_mac_tc(d, pt, G, (const uint32_t*)model, c->acc, st);
@@ -693,6 +696,7 @@ ephdc_status bfv_model_to_seeded(ephdc_ctx* c, const void* model, uint32_t* seed
   CHECK_CTX(c);
   CHECK_PTR(c, model, "model_dev");
   CHECK_PTR(c, seeded, "seeded_dev");
+  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0");
   return launched(c, ephdc::launch_model_to_seeded(c->dc, (const uint32_t*)model, seeded,
                                                    (cudaStream_t)stream),
                   "model_to_seeded");
@@ -703,6 +707,7 @@ ephdc_status bfv_model_from_seeded(ephdc_ctx* c, const uint32_t* seeded, uint64_
   CHECK_CTX(c);
   CHECK_PTR(c, seeded, "seeded_dev");
   CHECK_PTR(c, model, "model_dev");
+  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0");
   return launched(c, ephdc::launch_model_from_seeded(c->dc, seeded, seed, (uint32_t*)model,
                                                      (cudaStream_t)stream),
                   "model_from_seeded");
@@ -720,6 +725,7 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* c, const void* sk, const int8_t* H
   CHECK_PTR(c, model, "model_dev");
   if (!dmax) return fail(c, EPHDC_EINVAL, "dmax is NULL");
   const DevCtx& d = c->dc;
+  if (d.layout) return fail(c, EPHDC_EUNSUPPORTED, "the noise-growth trial needs layout 0");
   if (d.k != 1 || d.k_in != 1 || d.r != 1)
     return fail(c, EPHDC_EUNSUPPORTED, "needs one class and the layout k_in = 1, r = 1");
   if (B < 1 || (uint32_t)B > d.cap || (uint32_t)B > c->prm.max_batch)
@@ -757,6 +763,7 @@ ephdc_status bfv_encrypt_queries(ephdc_ctx* c, const int8_t* H, int32_t B, const
   CHECK_CTX(c);
   CHECK_PTR(c, H, "H_dev");
   CHECK_PTR(c, sk, "sk_dev");
+  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the server-side variant needs layout 0");
   CHECK_PTR(c, ctq, "query_ct_dev");
   CHECK_B(c, B);
   cudaError_t e;
@@ -773,6 +780,7 @@ ephdc_status bfv_encode_model_plain(ephdc_ctx* c, const int8_t* classes, uint32_
   CHECK_CTX(c);
   CHECK_PTR(c, classes, "class_hv_dev");
   CHECK_PTR(c, mm, "model_plain_dev");
+  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the server-side variant needs layout 0");
   return launched(c, ephdc::launch_encode_model_plain(c->dc, classes, mm, (cudaStream_t)stream),
                   "encode_model_plain");
 }
@@ -782,6 +790,7 @@ ephdc_status bfv_ctpt_similarity(ephdc_ctx* c, const uint32_t* ctq, int32_t B, c
   CHECK_CTX(c);
   CHECK_PTR(c, ctq, "query_ct_dev");
   CHECK_PTR(c, mm, "model_plain_dev");
+  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the server-side variant needs layout 0");
   CHECK_PTR(c, out, "out_ct_dev");
   if (c->dc.logr) CHECK_PTR(c, gk, "gk_dev");
   CHECK_B(c, B);
@@ -858,13 +867,49 @@ ephdc_status ephdc_plain_to_host_coeff(ephdc_ctx* c, const uint32_t* pt, int32_t
   CHECK_PTR(c, pt, "pt_dev");
   if (!host || count < 1) return fail(c, EPHDC_EINVAL, "bad host buffer or count");
   const DevCtx& d = c->dc;
+  if (d.layout && count % d.P)
+    return fail(c, EPHDC_EINVAL, "with the blocked layout count must be groups * P");
   const size_t words = (size_t)count * d.L * d.n;
   uint32_t* tmp = nullptr;
+  uint32_t* std_pt = nullptr;
   if (cudaMalloc(&tmp, words * 4) != cudaSuccess) return fail(c, EPHDC_ENOMEM, "cudaMalloc");
-  cudaError_t e = ephdc::launch_to_coeff(d, pt, tmp, count, 1, (int)(d.L * d.n), (int)d.n, 0, 0);
+  cudaError_t e = cudaSuccess;
+  if (d.layout) {  // blocked [L][n/4][G][P][4] -> [G][P][L][n]
+    e = cudaMalloc(&std_pt, words * 4);
+    if (e == cudaSuccess) e = ephdc::launch_unblock(d, pt, std_pt, count / d.P, d.P, 0);
+  }
+  if (e == cudaSuccess)
+    e = ephdc::launch_to_coeff(d, d.layout ? std_pt : pt, tmp, count, 1, (int)(d.L * d.n),
+                               (int)d.n, 0, 0);
   if (e == cudaSuccess) e = cudaMemcpy(host, tmp, words * 4, cudaMemcpyDeviceToHost);
   cudaFree(tmp);
+  if (std_pt) cudaFree(std_pt);
   return cuda_status(c, e, "plain_to_host_coeff");
+}
+
+ephdc_status ephdc_model_to_host_coeff(ephdc_ctx* c, const void* model, uint32_t* host) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, model, "model_dev");
+  if (!host) return fail(c, EPHDC_EINVAL, "host is NULL");
+  const DevCtx& d = c->dc;
+  const int count = (int)(d.P * d.Kp);
+  const size_t words = (size_t)count * 2 * d.L * d.n;
+  uint32_t* tmp = nullptr;
+  uint32_t* std_model = nullptr;
+  if (cudaMalloc(&tmp, words * 4) != cudaSuccess) return fail(c, EPHDC_ENOMEM, "cudaMalloc");
+  cudaError_t e = cudaSuccess;
+  if (d.layout) {  // blocked [L][n/4][P][O][4] -> [P][O][L][n]
+    e = cudaMalloc(&std_model, words * 4);
+    if (e == cudaSuccess)
+      e = ephdc::launch_unblock(d, (const uint32_t*)model, std_model, d.P, 2 * d.Kp, 0);
+  }
+  if (e == cudaSuccess)
+    e = ephdc::launch_to_coeff(d, d.layout ? std_model : (const uint32_t*)model, tmp, count, 2,
+                               (int)(2 * d.L * d.n), (int)d.n, 0, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host, tmp, words * 4, cudaMemcpyDeviceToHost);
+  cudaFree(tmp);
+  if (std_model) cudaFree(std_model);
+  return cuda_status(c, e, "model_to_host_coeff");
 }
 
 ephdc_status ephdc_sk_to_host(ephdc_ctx* c, const void* sk, int32_t* host) {
@@ -950,6 +995,11 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     if (v < 0 || v > 3) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1, 2 or 3");
     if (v == 3 && O > 32) return fail(c, EPHDC_EUNSUPPORTED, "tensor-core MAC needs k/k_in <= 16");
     c->mac_mode = (int)v;
+  } else if (!strcmp(knob, "layout")) {
+    if (v < 0 || v > 1) return fail(c, EPHDC_EINVAL, "layout must be 0 or 1");
+    if (v == 1 && O > 32)
+      return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs k/k_in <= 16");
+    c->dc.layout = (uint32_t)v;
   } else if (!strcmp(knob, "ntt_plan")) {
     if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "ntt_plan must be 0, 1 or 2");
     c->dc.ntt_plan = (int32_t)v;
@@ -987,6 +1037,7 @@ int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
   if (!strcmp(knob, "mac_min_groups")) return c->mac_min_groups;
   if (!strcmp(knob, "mac_tc_min_groups")) return c->mac_tc_min_groups;
   if (!strcmp(knob, "ntt_plan")) return c->dc.ntt_plan;
+  if (!strcmp(knob, "layout")) return c->dc.layout;
   if (!strcmp(knob, "hdc_mode")) return c->dc.hdc_mode;
   if (!strcmp(knob, "mac_splits")) return c->mac_splits;
   if (!strcmp(knob, "mac_tile"))

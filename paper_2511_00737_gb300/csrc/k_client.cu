@@ -62,10 +62,19 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
     const ModP m = c.mq[l];
     const CentredLift lift{mb, thalf, m.p - t};
     ntt_fwd_io<LOGN, CentredLift, SmemSt, V>(wb, m, lift, SmemSt{wb});
-    uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
-    for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
-      const uint32_t* w = wb + padi(4 * k);  // the 4 words never straddle a pad word
-      dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
+    if (c.layout) {  // coefficient-blocked: 16 bytes per (coefficient block, g, i)
+      const uint32_t G = ((uint32_t)B + c.cap - 1) / c.cap;
+      uint4* dst = reinterpret_cast<uint4*>(pt);
+      for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
+        const uint32_t* w = wb + padi(4 * k);
+        dst[blk_index(N, G, c.P, g, i, l, 4 * k) >> 2] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    } else {
+      uint4* dst = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * N);
+      for (uint32_t k = threadIdx.x; k < N / 4; k += blockDim.x) {
+        const uint32_t* w = wb + padi(4 * k);  // the 4 words never straddle a pad word
+        dst[k] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
     }
     __syncthreads();
   }
@@ -76,19 +85,23 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
 // plaintext i multiplied by w^(floor(P/g) - floor(i/g)).  One CTA per plaintext.
 __global__ void __launch_bounds__(256) k_scale_plain(DevCtx c, uint32_t* __restrict__ pt) {
   const uint32_t gi = blockIdx.x;
-  const uint32_t i = gi % c.P;
+  const uint32_t i = gi % c.P, g = gi / c.P, G = gridDim.x / c.P;
   for (uint32_t l = 0; l < c.L; l++) {
     const uint32_t p = c.mq[l].p;
     const uint32_t w = scale_factor(c, l, c.P / c.scale_g - i / c.scale_g);
     const uint32_t wsh = (uint32_t)(((uint64_t)w << 32) / p);
     uint4* q = reinterpret_cast<uint4*>(pt + ((size_t)gi * c.L + l) * c.n);
     for (uint32_t k = threadIdx.x; k < c.n / 4; k += blockDim.x) {
-      uint4 v = q[k];
+      // 4 coefficients of one block: contiguous in either layout
+      uint4* qk = c.layout
+                      ? reinterpret_cast<uint4*>(pt) + (blk_index(c.n, G, c.P, g, i, l, 4 * k) >> 2)
+                      : q + k;
+      uint4 v = *qk;
       v.x = csub(mulshoup(v.x, w, wsh, p), p);
       v.y = csub(mulshoup(v.y, w, wsh, p), p);
       v.z = csub(mulshoup(v.z, w, wsh, p), p);
       v.w = csub(mulshoup(v.w, w, wsh, p), p);
-      q[k] = v;
+      *qk = v;
     }
   }
 }

@@ -10,22 +10,24 @@
 // products are at most 2^14 in magnitude, at most 4 of them share an (i, s), and a
 // window of 256 plaintexts keeps every fp32 partial sum within 2^24.
 //
-// Shifted operand: the model digits of coefficient k are stored as 10 blocks of 32
-// rows (one row per output o), block t holding digit t - 3 (blocks 0-2 and 7-9 stay
-// zero).  The A operand of digit u is the 128-row window starting at block 3 - u
-// (rows (s, o), s = 0..3) or 7 - u (s = 4..7), so one MMA per (u, window) with the
-// plaintext digit d_u as B (N = 64 groups) adds exactly the products with u + v = s
+// Shifted operand: the model digits of a coefficient are 4 blocks of 32 rows (one row
+// per output o), block v holding digit e_v, with 3 zero blocks before and after.  The
+// A operand of plaintext digit u is the 128-row window starting u blocks before digit
+// 0 (rows (s, o), s = 0..3) or 4 - u blocks after it (s = 4..7), so one MMA per
+// (u, window) with d_u as B (N = 64 groups) adds exactly the products with u + v = s
 // into accumulator row (s, o).  7 MMAs of M = 128, N = 64, K = 16 per coefficient and
 // 16 plaintexts; the accumulators of one coefficient take 128 TMEM columns, so a CTA
 // holds 4 coefficients (all 512 columns) and every global read is a 16-byte piece.
 //
-// One CTA: limb l, 4 consecutive coefficients, one block of 64 groups, all outputs
-// (O <= 32), all plaintexts.  Each thread prefetches its pieces of the next chunks
-// into registers, splits them into digits in shared memory (two operand buffers), one
-// thread issues the 28 MMAs of a chunk and commits to the buffer's mbarrier.  After
-// each window the 8 warps read the accumulators out of TMEM, weight S_s by
-// 2^(8s) mod q_l, sum over s across warps in shared memory and add into per-CTA
-// accumulators mod q_l.  All waits are bounded.
+// Persistent CTAs (one per SM) walk tiles (limb l, 4 consecutive coefficients, a block
+// of 64 groups; all outputs O <= 32, all plaintexts) as one sequence of 16-plaintext
+// steps.  Each thread copies its 16-byte pieces of the step NS - 1 ahead into a
+// shared-memory ring with cp.async, splits its pieces of the current step into digits
+// (two operand buffers), and thread 0 issues the step's 28 MMAs and commits to the
+// buffer's mbarrier.  After each window the 8 warps read the accumulators out of TMEM,
+// weight S_s by 2^(8s) mod q_l, sum over s across warps in shared memory and add into
+// accumulators mod q_l held in registers; a tile's last window stores them.  All waits
+// are bounded.
 #include <cuda_fp16.h>
 
 #include "ephdc_internal.cuh"
@@ -33,25 +35,30 @@
 namespace {
 
 constexpr int THREADS = 256;
-constexpr int KB = 4;                      // coefficients per CTA
-constexpr int GN = 64;                     // groups per CTA = MMA N
+constexpr int KB = 4;                      // coefficients per tile
+constexpr int GN = 64;                     // groups per tile = MMA N
 constexpr int OR = 32;                     // output rows per digit block (O <= 32)
-constexpr int KC = 16;                     // plaintexts per chunk = MMA K
-constexpr int WIN = 16;                    // chunks per exact window (256 plaintexts)
-constexpr int ZB = 10;                     // digit blocks of the shifted model operand
-constexpr int ZBLK = OR * KC * 2;          // one block: 32 rows x 16 halves = 1 KB
-constexpr int Z_BYTES = ZB * ZBLK;         // per coefficient
+constexpr int KC = 16;                     // plaintexts per step = MMA K
+constexpr int WIN = 16;                    // steps per exact window (256 plaintexts)
+constexpr int ZBLK = OR * KC * 2;          // one digit block: 32 rows x 16 halves = 1 KB
+// model digit blocks: 3 zero blocks, then per coefficient 4 digit blocks and 3 zero
+// blocks (the zeros after one coefficient are the zeros before the next)
+constexpr int ZBLOCKS = 3 + KB * 7;
+__host__ __device__ constexpr int zdigit0(int j) { return 3 + 7 * j; }
 constexpr int BT_BYTES = GN * KC * 2;      // plaintext digit tile, per (coefficient, u)
-constexpr int A_REGION = KB * Z_BYTES;     // 40 KB
+constexpr int A_REGION = ZBLOCKS * ZBLK;   // 31 KB
 constexpr int B_REGION = KB * 4 * BT_BYTES;  // 32 KB
 constexpr int OPS_BYTES = A_REGION + B_REGION;
-constexpr int NBUF = 2;
-constexpr int ACC_WORDS = KB * GN * OR;    // per-CTA accumulators mod q_l
+constexpr int NBUF = 2;                    // operand buffers
+constexpr int NS = 4;                      // cp.async ring stages of raw pieces
+constexpr int RAW_PT = GN * KC * 16;       // 16 KB: pieces (g, i)
+constexpr int RAW_BYTES = RAW_PT + KC * OR * 16;  // + 8 KB: pieces (i, o)
 constexpr int TCOLS = 512;
 // kind::f16 instruction descriptor: D = f32, A = B = f16, both K-major, N = 64, M = 128
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(GN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-constexpr size_t SMEM = 1024 + NBUF * OPS_BYTES + ACC_WORDS * 4 + 64;
+constexpr size_t SMEM = 1024 + NBUF * OPS_BYTES + NS * RAW_BYTES + 64;
 static_assert(B_REGION >= 4 * GN * OR * 4, "the read-out staging lives in a B region");
+static_assert(SMEM <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -109,12 +116,11 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* v) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
-__device__ __forceinline__ uint4 ldg_stream(const uint32_t* p) {
-  uint4 v;
-  asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];\n"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
+// 16-byte global -> shared copy, zero-filled when !ok (src must still be a valid address)
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(ok ? 16 : 0)
+               : "memory");
 }
 // signed digit u of two residues as the two fp16 halves: xb, yb are the residues plus
 // 0x80808080, so byte u is d_u + 128; the byte lands in the mantissa of 1024.0
@@ -138,6 +144,7 @@ __device__ __forceinline__ uint32_t comp(const uint4& v, int j) {
 
 }  // namespace
 
+
 namespace {
 
 __global__ void __launch_bounds__(THREADS, 1) k_mac_tc(DevCtx c, const uint32_t* __restrict__ pt,
@@ -146,24 +153,23 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_tc(DevCtx c, const uint32_t*
                                                        uint32_t* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* ops = sm;                                           // [NBUF][A_REGION | B_REGION]
-  uint32_t* acc = (uint32_t*)(sm + NBUF * OPS_BYTES);          // [KB][GN][OR], mod q_l
-  uint64_t* bars = (uint64_t*)(acc + ACC_WORDS);               // MMA done, per buffer
+  uint8_t* ops = sm;                                         // [NBUF][A_REGION | B_REGION]
+  uint8_t* ring = sm + NBUF * OPS_BYTES;                     // [NS][RAW_BYTES]
+  uint64_t* bars = (uint64_t*)(ring + NS * RAW_BYTES);       // MMA done, per buffer
   uint32_t* tslot = (uint32_t*)(bars + NBUF);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t l = blockIdx.y, k0 = blockIdx.x * KB;
-  const int g0 = blockIdx.z * GN;
   const int O = 2 * (int)c.Kp;
   const uint32_t P = c.P, n = c.n, L = c.L;
-  const ModP m = c.mq[l];
   const int nch = (int)((P + KC - 1) / KC);
+  const int kblocks = (int)(n / KB), gblocks = (G + GN - 1) / GN;
+  const int tiles = kblocks * (int)L * gblocks;
+  const int my_tiles = tiles > (int)blockIdx.x ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int steps = my_tiles * nch;
 
-  {  // zero both operand buffers (the zero digit blocks of the model operand stay
-     // zero) and the accumulators
+  {  // zero both operand buffers (the zero digit blocks of the model operand stay zero)
     uint4* z = reinterpret_cast<uint4*>(ops);
     for (int i = tid; i < NBUF * OPS_BYTES / 16; i += THREADS) z[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < ACC_WORDS; i += THREADS) acc[i] = 0;
   }
   if (tid == 0) {
     for (int b = 0; b < NBUF; b++)
@@ -182,101 +188,147 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_tc(DevCtx c, const uint32_t*
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  // Pieces of a chunk: plaintext rows (g, i) of group g = tid / 4 and plaintexts
+  // tile t: coefficient block t % kblocks (fastest, so CTAs running side by side read
+  // neighbouring 16-byte pieces of the same sectors), then limb, then group block
+  struct Tile {
+    uint32_t l, k0;
+    int g0;
+  };
+  auto tile_of = [&](int s) -> Tile {
+    const int t = (int)blockIdx.x + (s / nch) * (int)gridDim.x;
+    const int kb = t % kblocks, rest = t / kblocks;
+    return Tile{(uint32_t)(rest % (int)L), (uint32_t)(kb * KB), (rest / (int)L) * GN};
+  };
+
+  // Pieces of a step: plaintext rows (g, i) of group g = tid / 4 and plaintexts
   // 4 (tid % 4) .. + 3; model rows (i, o) of output o = 8 (warp % 4) + lane / 4 and
   // plaintexts 8 (warp / 4) + 2 (lane % 4) .. + 1.  Each piece is the 16 bytes of the
-  // CTA's 4 coefficients; rows outside the batch read as zero.
+  // tile's 4 coefficients; rows outside the batch are zero-filled.  Every thread reads
+  // back only the pieces it copied, so its own cp.async wait orders them.
   const int pg = tid >> 2, pq = (tid & 3) * 4;
-  const bool pvalid = g0 + pg < G;
-  const uint32_t* pbase = pt + ((size_t)(pvalid ? g0 + pg : 0) * P * L + l) * n + k0;
-  const size_t pstep = (size_t)L * n;
   const int mo = (warp & 3) * 8 + (lane >> 2), mi = (warp >> 2) * 8 + 2 * (lane & 3);
-  const bool mvalid = mo < O;
-  const uint32_t* mbase = model + ((size_t)(mvalid ? mo : 0) * L + l) * n + k0;
-  const size_t mstep = (size_t)O * L * n;
-
-  auto load = [&](int ch, uint4 (&R)[6]) {
+  const size_t pstep = (size_t)L * n, mstep = (size_t)O * L * n;
+  auto issue = [&](int s) {
+    if (s < steps) {
+      const Tile T = tile_of(s);
+      const int ch = s % nch;
+      const uint32_t dst = smem_u32(ring + (s % NS) * RAW_BYTES);
+      const bool gok = T.g0 + pg < G;
+      const uint32_t gg = gok ? T.g0 + pg : 0;
+      // layout 0: plaintext (g, i) at ((g P + i) L + l) n; layout 1: the tile's 16 bytes
+      // of every (g, i) of a coefficient block are contiguous, 4 words per i
+      const uint32_t* pb = c.layout ? pt + blk_index(n, G, P, gg, 0, T.l, T.k0)
+                                    : pt + ((size_t)gg * P * L + T.l) * n + T.k0;
+      const size_t ps = c.layout ? 4 : pstep;
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-      const uint32_t i = (uint32_t)(ch * KC + pq + e);
-      R[e] = (pvalid && i < P) ? ldg_stream(pbase + i * pstep) : make_uint4(0, 0, 0, 0);
-    }
+      for (int e = 0; e < 4; e++) {
+        const uint32_t i = (uint32_t)(ch * KC + pq + e);
+        const bool ok = gok && i < P;
+        cp_async16(dst + (pg * KC + pq + e) * 16, ok ? pb + i * ps : pt, ok);
+      }
+      const bool ook = mo < O;
+      const uint32_t oo = ook ? mo : 0;
+      const uint32_t* mb = c.layout ? model + blk_index(n, P, O, 0, oo, T.l, T.k0)
+                                    : model + ((size_t)oo * L + T.l) * n + T.k0;
+      const size_t ms = c.layout ? (size_t)O * 4 : mstep;
 #pragma unroll
-    for (int e = 0; e < 2; e++) {
-      const uint32_t i = (uint32_t)(ch * KC + mi + e);
-      R[4 + e] = (mvalid && i < P) ? ldg_stream(mbase + i * mstep) : make_uint4(0, 0, 0, 0);
+      for (int e = 0; e < 2; e++) {
+        const uint32_t i = (uint32_t)(ch * KC + mi + e);
+        const bool ok = ook && i < P;
+        cp_async16(dst + RAW_PT + ((mi + e) * OR + mo) * 16, ok ? mb + i * ms : model, ok);
+      }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
   };
-  // registers -> signed fp16 digits in operand buffer `buf`
-  auto split = [&](const uint4 (&R)[6], int buf) {
+  // this thread's raw pieces of step s -> signed fp16 digits in operand buffer `buf`
+  auto split = [&](int s, int buf) {
+    const uint8_t* R = ring + (s % NS) * RAW_BYTES;
+    uint4 x[4], y[2];
+#pragma unroll
+    for (int e = 0; e < 4; e++) x[e] = *reinterpret_cast<const uint4*>(R + (pg * KC + pq + e) * 16);
+#pragma unroll
+    for (int e = 0; e < 2; e++)
+      y[e] = *reinterpret_cast<const uint4*>(R + RAW_PT + ((mi + e) * OR + mo) * 16);
     uint8_t* A = ops + buf * OPS_BYTES;
     uint8_t* B = A + A_REGION;
 #pragma unroll
     for (int j = 0; j < KB; j++) {
-      const uint32_t x0 = comp(R[0], j) + 0x80808080u, x1 = comp(R[1], j) + 0x80808080u;
-      const uint32_t x2 = comp(R[2], j) + 0x80808080u, x3 = comp(R[3], j) + 0x80808080u;
+      const uint32_t x0 = comp(x[0], j) + 0x80808080u, x1 = comp(x[1], j) + 0x80808080u;
+      const uint32_t x2 = comp(x[2], j) + 0x80808080u, x3 = comp(x[3], j) + 0x80808080u;
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const uint2 v = make_uint2(sdigit_pair(x0, x1, u), sdigit_pair(x2, x3, u));
         *reinterpret_cast<uint2*>(B + (j * 4 + u) * BT_BYTES + op_off(pg, pq)) = v;
       }
-      const uint32_t y0 = comp(R[4], j) + 0x80808080u, y1 = comp(R[5], j) + 0x80808080u;
+      const uint32_t y0 = comp(y[0], j) + 0x80808080u, y1 = comp(y[1], j) + 0x80808080u;
 #pragma unroll
       for (int v = 0; v < 4; v++)
-        *reinterpret_cast<uint32_t*>(A + j * Z_BYTES + (3 + v) * ZBLK + op_off(mo, mi)) =
+        *reinterpret_cast<uint32_t*>(A + (zdigit0(j) + v) * ZBLK + op_off(mo, mi)) =
             sdigit_pair(y0, y1, v);
     }
   };
 
-  // read-out of a finished window: warp w reads TMEM lanes 32 (w % 4) + o (rows
-  // s = w % 4 and s = 4 + w % 4 of output o) for groups 32 (w / 4) .. + 31, weights them
-  // by 2^(8s) mod q_l, and the 4 lane quarters are summed through shared memory
-  const int qd = warp & 3, hf = warp >> 2;
-  uint32_t W0 = 1, W1 = 0;
-  for (int s = 0; s < qd; s++) W0 = mulm(W0, 256u, m);
-  if (qd < 3) {
-    W1 = W0;
-    for (int s = 0; s < 4; s++) W1 = mulm(W1, 256u, m);
-  }
-  // |S0 W0 + S1 W1| < 2^55: adding a multiple of q_l above 2^56 keeps it non-negative
-  const uint64_t OFF = ((1ull << 56) / m.p + 1) * m.p;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(ops + A_REGION);  // [4 qd][GN][OR]
-  auto readout = [&]() {
-#pragma unroll 1
-    for (int j = 0; j < KB; j++) {
-      uint32_t v0[32], v1[32];
-      const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(j * 2 * GN + hf * 32);
-      tc_ld32(ta, v0);
-      tc_ld32(ta + GN, v1);
+  // per-thread accumulators mod q_l: pairs idx = tid + 256 r = g * 32 + o (group g,
+  // output o) of each coefficient j of the current tile
+  uint32_t acc[KB][8];
 #pragma unroll
-      for (int e = 0; e < 32; e++) {
-        const int64_t s = (int64_t)__float2int_rn(__uint_as_float(v0[e])) * W0 +
-                          (int64_t)__float2int_rn(__uint_as_float(v1[e])) * W1;
-        stage[(qd * GN + hf * 32 + e) * OR + lane] = red64((uint64_t)(s + (int64_t)OFF), m.p, m.mu);
+  for (int j = 0; j < KB; j++)
+#pragma unroll
+    for (int r = 0; r < 8; r++) acc[j][r] = 0;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(ops + A_REGION);  // [4 qd][GN][OR]
+  // window read-out: warp w reads TMEM lanes 32 (w % 4) + o (rows s = w % 4 and
+  // s = 4 + w % 4 of output o) for groups 32 (w / 4) .. + 31, weights them by
+  // 2^(8s) mod q_l, and the 4 lane quarters are summed through shared memory
+  const int qd = warp & 3, hf = warp >> 2;
+  auto readout = [&](const ModP& m) {
+    uint32_t W0 = 1, W1 = 0;
+    for (int s = 0; s < qd; s++) W0 = mulm(W0, 256u, m);
+    if (qd < 3) {
+      W1 = W0;
+      for (int s = 0; s < 4; s++) W1 = mulm(W1, 256u, m);
+    }
+    // |S0 W0 + S1 W1| < 2^55: adding a multiple of q_l above 2^56 keeps it non-negative
+    const int64_t OFF = (int64_t)(((1ull << 56) / m.p + 1) * m.p);
+#pragma unroll
+    for (int j = 0; j < KB; j++) {
+      {
+        uint32_t v0[32], v1[32];
+        const uint32_t ta = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(j * 2 * GN + hf * 32);
+        tc_ld32(ta, v0);
+        tc_ld32(ta + GN, v1);
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+          const int64_t v = (int64_t)__float2int_rn(__uint_as_float(v0[e])) * W0 +
+                            (int64_t)__float2int_rn(__uint_as_float(v1[e])) * W1 + OFF;
+          stage[(qd * GN + hf * 32 + e) * OR + lane] = red64((uint64_t)v, m.p, m.mu);
+        }
       }
       __syncthreads();
-      uint32_t* a = acc + j * GN * OR;
-      for (int idx = tid; idx < GN * OR; idx += THREADS) {
-        const uint64_t t = (uint64_t)a[idx] + stage[idx] + stage[GN * OR + idx] +
+#pragma unroll
+      for (int r = 0; r < 8; r++) {
+        const int idx = tid + THREADS * r;
+        const uint64_t t = (uint64_t)acc[j][r] + stage[idx] + stage[GN * OR + idx] +
                            stage[2 * GN * OR + idx] + stage[3 * GN * OR + idx];
-        a[idx] = red64(t, m.p, m.mu);
+        acc[j][r] = red64(t, m.p, m.mu);
       }
       __syncthreads();
     }
   };
 
-  // Chunk ch: wait until its operand buffer's previous MMAs (chunk ch - 2) are done,
-  // split the prefetched pieces into it, prefetch chunk ch + 2, and after one block
-  // barrier thread 0 issues the chunk's MMAs.  At a window's end every thread waits
-  // for them, reads the window out and the next window restarts the accumulators.
+  // Step s: wait for its pieces and for its operand buffer's previous MMAs (step
+  // s - 2), split the pieces into it, start the copies of step s + NS - 1, and after
+  // one block barrier thread 0 issues the step's MMAs.  At a window's end every thread
+  // waits for them, reads the window out; the next window restarts the accumulators.
   bool alive = true;
-  auto step = [&](int ch, uint4 (&R)[6]) {
-    const int b = ch & 1;
-    if (ch >= 2 && alive &&
-        !mbar_wait(smem_u32(&bars[b]), ((ch - 2) >> 1) & 1, status, 13))
+  for (int s = 0; s < NS - 1; s++) issue(s);
+#pragma unroll 1
+  for (int s = 0; s < steps; s++) {
+    const int b = s & 1, ch = s % nch;
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2) : "memory");
+    if (s >= 2 && alive && !mbar_wait(smem_u32(&bars[b]), ((s - 2) >> 1) & 1, status, 13))
       alive = false;
-    if (alive) split(R, b);
-    if (ch + 2 < nch) load(ch + 2, R);
+    if (alive) split(s, b);
+    issue(s + NS - 1);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     alive = __syncthreads_and(alive);
     if (tid == 0 && alive) {
@@ -290,7 +342,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_tc(DevCtx c, const uint32_t*
           const uint32_t d = tmem + (uint32_t)((j * 2 + tile) * GN);
 #pragma unroll
           for (int u = tile; u < 4; u++) {
-            const uint32_t aa = a0 + j * Z_BYTES + ((tile ? 7 : 3) - u) * ZBLK;
+            const uint32_t aa = a0 + (zdigit0(j) + 4 * tile - u) * ZBLK;
             const uint32_t bb = b0 + (j * 4 + u) * BT_BYTES;
             tc_mma(d, sdesc_noswz(aa, 128, 256), sdesc_noswz(bb, 128, 256),
                    (first_of_window && u == tile) ? 0u : 1u);
@@ -300,33 +352,27 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_tc(DevCtx c, const uint32_t*
       tc_commit(smem_u32(&bars[b]));
     }
     if ((ch % WIN) == WIN - 1 || ch == nch - 1) {
-      const bool ok = alive && mbar_wait(smem_u32(&bars[b]), (ch >> 1) & 1, status, 14);
+      const bool ok = alive && mbar_wait(smem_u32(&bars[b]), (s >> 1) & 1, status, 14);
       alive = __syncthreads_and(ok);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      if (alive) readout();
+      const Tile T = tile_of(s);
+      if (alive) readout(c.mq[T.l]);
+      if (ch == nch - 1) {
+        // the tile's 4 consecutive coefficients of (group, output) as one 16-byte store
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+          const int g = (tid >> 5) + 8 * r, o = tid & 31;
+          if (alive && T.g0 + g < G && o < O)
+            *reinterpret_cast<uint4*>(out + (((size_t)(T.g0 + g) * O + o) * L + T.l) * n + T.k0) =
+                make_uint4(acc[0][r], acc[1][r], acc[2][r], acc[3][r]);
+#pragma unroll
+          for (int j = 0; j < KB; j++) acc[j][r] = 0;
+        }
+      }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     }
-  };
-
-  uint4 ra[6], rb[6];
-  load(0, ra);
-  if (nch > 1) load(1, rb);
-#pragma unroll 1
-  for (int ch = 0; ch < nch; ch += 2) {
-    step(ch, ra);
-    if (ch + 1 < nch) step(ch + 1, rb);
   }
-
-  __syncthreads();
-  // 4 consecutive coefficients of (group, output) as one 16-byte store
-  for (int idx = tid; idx < GN * OR; idx += THREADS) {
-    const int g = idx / OR, o = idx % OR;
-    if (g0 + g < G && o < O) {
-      const uint4 v = make_uint4(acc[idx], acc[GN * OR + idx], acc[2 * GN * OR + idx],
-                                 acc[3 * GN * OR + idx]);
-      *reinterpret_cast<uint4*>(out + (((size_t)(g0 + g) * O + o) * L + l) * n + k0) = v;
-    }
-  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   if (warp == 0)
@@ -342,10 +388,14 @@ namespace ephdc {
 cudaError_t launch_mac_tc(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                           uint32_t* acc, cudaStream_t st) {
   if (2 * (int)c.Kp > OR || c.n % KB) return cudaErrorNotSupported;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_mac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_mac_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid(c.n / KB, c.L, (G + GN - 1) / GN);
+  const long long tiles = (long long)(c.n / KB) * c.L * ((G + GN - 1) / GN);
+  const int grid = (int)(tiles < sms ? tiles : sms);  // persistent: one CTA per SM
   k_mac_tc<<<grid, THREADS, SMEM, st>>>(c, pt, model, acc, G, c.status);
   return cudaGetLastError();
 }

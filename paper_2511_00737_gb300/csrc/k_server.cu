@@ -118,11 +118,18 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
   const uint32_t* s = sk + (size_t)l * c.n;
   uint32_t* c0 = model + ((size_t)(cidx * 2 + 0) * c.L + l) * c.n;
   uint32_t* c1 = model + ((size_t)(cidx * 2 + 1) * c.L + l) * c.n;
+  const uint32_t O = 2 * c.Kp;
   for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) {
     const uint32_t a = ab[padi(x)];
     uint32_t v = subm(eb[padi(x)], mulm(a, s[x], m), m.p);
-    c0[x] = addm(v, mb[padi(x)], m.p);
-    c1[x] = a;
+    v = addm(v, mb[padi(x)], m.p);
+    if (c.layout) {  // outputs o = j' * 2 + poly of plaintext i
+      model[blk_index(c.n, c.P, O, i, jp * 2, l, x)] = v;
+      model[blk_index(c.n, c.P, O, i, jp * 2 + 1, l, x)] = a;
+    } else {
+      c0[x] = v;
+      c1[x] = a;
+    }
   }
 }
 
@@ -318,6 +325,20 @@ __global__ void __launch_bounds__(512) k_ntt_natural(DevCtx c, uint32_t limb, ui
   }
 }
 
+// blocked [L][n/4][A][B][4] -> standard [A][B][L][n] (host-format conversions)
+__global__ void k_unblock(DevCtx c, const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                          uint32_t A, uint32_t B, size_t words) {
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < words;
+       x += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = (uint32_t)(x % c.n);
+    size_t rest = x / c.n;
+    const uint32_t l = (uint32_t)(rest % c.L);
+    rest /= c.L;
+    const uint32_t b = (uint32_t)(rest % B), a = (uint32_t)(rest / B);
+    dst[x] = src[blk_index(c.n, A, B, a, b, l, k)];
+  }
+}
+
 }  // namespace
 
 namespace ephdc {
@@ -378,6 +399,14 @@ cudaError_t launch_decrypt_phases(const DevCtx& c, uint32_t* xbuf, int count, in
   if (e != cudaSuccess) return e;
   k_dec_round<<<dim3(count, (c.n + 255) / 256), 256, 0, st>>>(c, xbuf);
   k_dec_scores<<<count, ntt_threads(c), s1, st>>>(c, xbuf, B, scores);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unblock(const DevCtx& c, const uint32_t* src, uint32_t* dst, uint32_t A,
+                           uint32_t B, cudaStream_t st) {
+  const size_t words = (size_t)A * B * c.L * c.n;
+  const unsigned blocks = (unsigned)((words + 255) / 256 < 152 * 32 ? (words + 255) / 256 : 152 * 32);
+  k_unblock<<<blocks, 256, 0, st>>>(c, src, dst, A, B, words);
   return cudaGetLastError();
 }
 

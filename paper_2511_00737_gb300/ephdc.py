@@ -62,6 +62,7 @@ _SIGS = {
     "ephdc_sk_to_host": (ctypes.c_int, [_VP, _VP, _VP]),
     "ephdc_gk_to_host_coeff": (ctypes.c_int, [_VP, _VP, _VP]),
     "ephdc_plain_to_host_coeff": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP]),
+    "ephdc_model_to_host_coeff": (ctypes.c_int, [_VP, _VP, _VP]),
     "ephdc_ntt_natural": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP, ctypes.c_int32, ctypes.c_int,
                                          _VP]),
     "bfv_ptct_similarity_noalloc": (ctypes.c_int, [_VP, _VP, ctypes.c_int32, _VP, _VP, _VP,
@@ -386,6 +387,13 @@ class Context:
         if self.logr:
             _check(self.ctx, lib().ephdc_gk_to_host_coeff(self.ctx, _ptr(gk, "gk"),
                                                           host.ctypes.data_as(_VP)))
+        return host
+
+    def model_to_host_coeff(self, model):
+        import numpy as np
+        host = np.zeros((self.P, self.Kp, 2, self.L, self.n), np.uint32)
+        _check(self.ctx, lib().ephdc_model_to_host_coeff(self.ctx, _ptr(model, "model"),
+                                                         host.ctypes.data_as(_VP)))
         return host
 
     def plain_to_host_coeff(self, pt, count):
