@@ -62,7 +62,10 @@ def parse():
                     help="override the workload's batch size (profiling of smaller cases)")
     ap.add_argument("--layout", type=int, default=-1,
                     help="storage layout of plaintexts and model (0 standard, 1 "
-                         "coefficient-blocked); default: 1 for n >= 16384")
+                         "coefficient-blocked); default 0")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="encode and accumulate this many plaintext indices of every group "
+                         "at a time (0 = the whole pass at once)")
     ap.add_argument("--no-legs", action="store_true",
                     help="time only the headline workload (not clients64, serve, dense65536)")
     return ap.parse_args()
@@ -259,9 +262,10 @@ def run_ours(args, w, B):
         from paper_2511_00737_gb300 import batching as BT
     # packed multi-client steps replay whole groups, so reserve full groups
     ctx = E.Context.for_workload(w, max_batch=(-(-B // cap) * cap) if multi else B)
-    # storage layout of plaintexts and model: coefficient-blocked (read by the
-    # tensor-core product) for the dense shapes, unless forced
-    layout = args.layout if args.layout >= 0 else int(w.n >= 16384 and 2 * (w.k // w.k_in) <= 32)
+    # storage layout of plaintexts and model (standard unless forced: at dense65536 the
+    # blocked layout's faster tensor-core product is offset by the encoder's scattered
+    # 16-byte stores)
+    layout = max(0, args.layout)
     ctx.tune_set("layout", layout)
     if args.mac_mode >= 0:
         ctx.tune_set("mac_mode", args.mac_mode)
@@ -314,6 +318,8 @@ def run_ours(args, w, B):
             cx.tune_set("layout", layout)  # the shared model's layout
             if tuned:
                 AT.apply(cx, tuned)
+        for cx in ctxs:
+            cx.tune_set("chunk", args.chunk)
             if args.hdc_mode >= 0:
                 cx.tune_set("hdc_mode", args.hdc_mode)
         outs = [out] + [cx.out_ct(B) for cx in ctxs[1:]]
@@ -490,6 +496,8 @@ def run_ours(args, w, B):
                 "parity": parity}
         if not multi:
             line["config"]["streams"] = S
+            if args.chunk:
+                line["config"]["chunk_plaintexts"] = args.chunk
             line["config"]["batches_per_step"] = pack
             line["config"]["batch"] = batch
         line["config"]["storage_layout"] = "coefficient-blocked" if layout else "standard"

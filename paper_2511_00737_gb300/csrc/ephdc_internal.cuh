@@ -680,8 +680,11 @@ struct GatherTable {
   int32_t count;
 };
 cudaError_t launch_gather_widen(const DevCtx& c, const GatherTable& t, cudaStream_t st);
+// ni > 0: plaintexts i0 .. i0 + ni - 1 of every group only, into a buffer of ni
+// plaintexts per group
 cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_t* pt,
-                                cudaStream_t st);
+                                cudaStream_t st, uint32_t i0 = 0,
+                               uint32_t ni = 0);
 cudaError_t launch_mac(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                        uint32_t* partial, int splits, uint32_t* acc, cudaStream_t st);
 // acc[x] = sum over splits of partial[split][x] mod q_l, x < words
@@ -692,8 +695,11 @@ cudaError_t launch_mac_reduce(const DevCtx& c, const uint32_t* partial, int spli
 struct MacTiling {
   int gt, ot, gc, ic;
 };
+// pP > 0: a chunk of a pass (plaintexts mi0 .. mi0 + cnt - 1 of the model against a
+// buffer of pP plaintexts per group), added into acc when accum != 0
 cudaError_t launch_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
-                             uint32_t* acc, const MacTiling& t, cudaStream_t st);
+                             uint32_t* acc, const MacTiling& t, cudaStream_t st, int pP = 0,
+                             int mi0 = 0, int cnt = 0, int accum = 0);
 // the same accumulators through the exact byte-split tensor-core product (k/k_in <= 16)
 cudaError_t launch_mac_tc(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                           uint32_t* acc, cudaStream_t st);

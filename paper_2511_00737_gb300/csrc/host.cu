@@ -122,11 +122,13 @@ struct ephdc_ctx {
   // plaintext ranges), 2 = tiled multi-group
   int mac_mode = 0;
   int mac_min_groups = 4;  // automatic mode: tiled from this many groups on
-  // automatic mode: tensor cores from this many groups on (off unless tuned: on this
-  // part the byte-split product does not yet beat the tiled CUDA-core kernel)
+  // automatic mode: tensor cores from this many groups on (off unless tuned)
   int mac_tc_min_groups = 1 << 30;
   int mac_splits = 0;      // streaming: split count cap (0 = heuristic)
   ephdc::MacTiling tile = {4, 8, 32, 8};
+  // ephdc_infer with the tiled MAC: encode and accumulate this many plaintext indices
+  // of every group at a time into a reused buffer (0 = the whole pass at once)
+  int chunk = 0;
 };
 
 static cudaEvent_t take_event(ephdc_ctx* c) {
@@ -821,6 +823,28 @@ ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_
     e = ephdc::launch_hdc_encode(c->dc, X, Wt, B, c->H, st);
   }
   if (e != cudaSuccess) return launched(c, e, "hdc_encode");
+  const DevCtx& d = c->dc;
+  const int G = (int)groups_for(c, B);
+  const bool tiled = c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups &&
+                                          G < c->mac_tc_min_groups);
+  if (c->chunk > 0 && (uint32_t)c->chunk < d.P && tiled && !d.layout && !d.scale_g) {
+    // plaintext-index chunks: each chunk's plaintexts of all G groups are encoded into
+    // the start of the plaintext buffer and accumulated from there while they are
+    // still in L2 (the whole pass writes and reads every plaintext through HBM once)
+    for (uint32_t i0 = 0; i0 < d.P && e == cudaSuccess; i0 += (uint32_t)c->chunk) {
+      const uint32_t ni = d.P - i0 < (uint32_t)c->chunk ? d.P - i0 : (uint32_t)c->chunk;
+      {
+        StageTimer tm(c, EPHDC_STAGE_ENCODE, st, 1);
+        e = ephdc::launch_encode_plain(d, c->H, B, c->pt, st, i0, ni);
+      }
+      if (e != cudaSuccess) break;
+      StageTimer tm(c, EPHDC_STAGE_MAC, st, 1);
+      e = ephdc::launch_mac_tiled(d, c->pt, G, (const uint32_t*)model, c->acc, c->tile, st,
+                                  (int)ni, (int)i0, (int)ni, i0 > 0);
+    }
+    if (e != cudaSuccess) return launched(c, e, "chunked encode + mac");
+    return rotate_export(c, G, gk, out, st);
+  }
   {
     StageTimer tm(c, EPHDC_STAGE_ENCODE, st, c->dc.scale_g ? 2 : 1);
     e = ephdc::launch_encode_plain(c->dc, c->H, B, c->pt, st);
@@ -995,6 +1019,9 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     if (v < 0 || v > 3) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1, 2 or 3");
     if (v == 3 && O > 32) return fail(c, EPHDC_EUNSUPPORTED, "tensor-core MAC needs k/k_in <= 16");
     c->mac_mode = (int)v;
+  } else if (!strcmp(knob, "chunk")) {
+    if (v < 0) return fail(c, EPHDC_EINVAL, "chunk must be >= 0");
+    c->chunk = (int)v;
   } else if (!strcmp(knob, "layout")) {
     if (v < 0 || v > 1) return fail(c, EPHDC_EINVAL, "layout must be 0 or 1");
     if (v == 1 && O > 32)
@@ -1038,6 +1065,7 @@ int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
   if (!strcmp(knob, "mac_tc_min_groups")) return c->mac_tc_min_groups;
   if (!strcmp(knob, "ntt_plan")) return c->dc.ntt_plan;
   if (!strcmp(knob, "layout")) return c->dc.layout;
+  if (!strcmp(knob, "chunk")) return c->chunk;
   if (!strcmp(knob, "hdc_mode")) return c->dc.hdc_mode;
   if (!strcmp(knob, "mac_splits")) return c->mac_splits;
   if (!strcmp(knob, "mac_tile"))

@@ -40,13 +40,16 @@ struct CentredLift {
 // with 16-byte writes.  (The scaling operation, when on, is a separate pass.)
 template <int LOGN, int V>
 __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
-    k_encode_plain(DevCtx c, const int8_t* __restrict__ H, int B, uint32_t* __restrict__ pt) {
+    k_encode_plain(DevCtx c, const int8_t* __restrict__ H, int B, uint32_t* __restrict__ pt,
+                   uint32_t i0, uint32_t ni) {
   constexpr uint32_t N = 1u << LOGN;
   extern __shared__ uint32_t sm[];
   uint32_t* mb = sm;
   uint32_t* wb = sm + padded_words(N);
+  // block gi: plaintext i0 + gi % ni of group gi / ni, stored as plaintext gi of a
+  // buffer of ni plaintexts per group (the whole pass: i0 = 0, ni = P)
   const uint32_t gi = blockIdx.x;
-  const uint32_t g = gi / c.P, i = gi - g * c.P;
+  const uint32_t g = gi / ni, i = i0 + (gi - g * ni);
   // with cap r k_in = n, a full group and a full D-chunk write every slot exactly once
   const bool every_slot = c.cap * c.r * c.k_in == N && (g + 1) * c.cap <= (uint32_t)B &&
                           (i + 1) * c.r <= c.D;
@@ -188,11 +191,14 @@ __device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, ui
       : "r"(a), "r"(b));
 }
 
+// A chunked pass (several calls over plaintext ranges) reads plaintexts
+// [mi0, mi0 + cnt) of the model against a plaintext buffer of pP plaintexts per group
+// and adds into the accumulators (accum != 0) instead of overwriting them.
 template <int GT, int OT>
 __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __restrict__ pt,
                                                    const uint32_t* __restrict__ model,
                                                    uint32_t* __restrict__ acc, int G, int GC,
-                                                   int IC) {
+                                                   int IC, int pP, int mi0, int cnt, int accum) {
   extern __shared__ __align__(16) uint32_t sm[];
   const uint32_t l = blockIdx.y, k0 = blockIdx.x * 32;
   const int g0 = blockIdx.z * GC;
@@ -204,7 +210,8 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
   const int buf_words = IC * rows * 32;
   const uint32_t p = c.mq[l].p;
   const uint64_t mu = c.mq[l].mu;
-  const size_t n = c.n, L = c.L, P = c.P;
+  const size_t n = c.n, L = c.L, P = (size_t)pP;
+  const uint32_t CNT = (uint32_t)cnt;
 
   // copy slots: slot q = rr * 8 + piece (row rr of a staged plaintext index, 16-byte
   // piece, shared-memory word offset 4 q) belongs to thread q mod blockDim for every
@@ -223,10 +230,11 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
         const size_t stride = is_pt ? pt_stride : model_stride;
         const uint32_t* src =
             is_pt ? pt + ((size_t)(gok ? g0 + rr : 0) * P * L + l) * n + k0 + piece * 4
-                  : model + ((size_t)(rr - GC) * L + l) * n + k0 + piece * 4;
+                  : model + ((size_t)(rr - GC) * L + l) * n + k0 + piece * 4 +
+                        (size_t)mi0 * model_stride;
         src += (size_t)i0 * stride;
         for (int ii = 0; ii < IC; ii++, src += stride) {
-          const bool ok = gok && i0 + ii < P;
+          const bool ok = gok && i0 + ii < CNT;
           cp_async16_zfill(dst + ii * rows * 32 + 4 * q, ok ? src : pt, ok);
         }
       }
@@ -243,7 +251,7 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
 #pragma unroll
     for (int y = 0; y < OT; y++) alo[x][y] = ahi[x][y] = 0;
   const int gb = wg * GT, ob = wo * OT;
-  const int nchunks = (int)((P + IC - 1) / IC);
+  const int nchunks = (int)((CNT + IC - 1) / IC);
   load_chunk(0, 0);
   for (int ch = 0; ch < nchunks; ch++) {
     if (ch + 1 < nchunks) {
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
     }
     __syncthreads();
     const uint32_t* buf = sm + (ch & 1) * buf_words;
-    const int iend = min(IC, (int)P - ch * IC);
+    const int iend = min(IC, (int)CNT - ch * IC);
 #pragma unroll 3
     for (int ii = 0; ii < iend; ii++) {
       const uint32_t* rowp = buf + ii * rows * 32 + lane;
@@ -284,7 +292,8 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
 #pragma unroll
     for (int o = 0; o < OT; o++) {
       if (ob + o >= O) continue;
-      acc[(((size_t)gg * O + ob + o) * L + l) * n + k0 + lane] = alo[g][o];
+      uint32_t* a = acc + (((size_t)gg * O + ob + o) * L + l) * n + k0 + lane;
+      *a = accum ? csub(*a + alo[g][o], p) : alo[g][o];
     }
   }
 }
@@ -453,15 +462,20 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 namespace ephdc {
 
 cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_t* pt,
-                                cudaStream_t st) {
+                                cudaStream_t st, uint32_t i0, uint32_t ni) {
   const int G = (B + c.cap - 1) / c.cap;
+  if (ni == 0) {
+    i0 = 0;
+    ni = c.P;
+  }
+  if (ni != c.P && (c.layout || c.scale_g)) return cudaErrorNotSupported;
   const size_t smem = 2 * padded_words(c.n) * sizeof(uint32_t);
   EPHDC_DISPATCH_LOGN(c.logn, LG, {
     auto kern = c.ntt_plan == 1 ? k_encode_plain<LG, 1>
               : c.ntt_plan == 2 ? k_encode_plain<LG, 2> : k_encode_plain<LG, 0>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<G * c.P, ntt_threads(c), smem, st>>>(c, H, B, pt);
+    kern<<<G * ni, ntt_threads(c), smem, st>>>(c, H, B, pt, i0, ni);
   });
   if (c.scale_g) k_scale_plain<<<G * c.P, 256, 0, st>>>(c, pt);
   return cudaGetLastError();
@@ -470,7 +484,8 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
 // the tiled kernel's instantiations: (groups per warp, outputs per warp)
 template <int GT, int OT>
 static cudaError_t run_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
-                                 uint32_t* acc, int GC, int IC, cudaStream_t st) {
+                                 uint32_t* acc, int GC, int IC, int pP, int mi0, int cnt,
+                                 int accum, cudaStream_t st) {
   // IC <= 15 keeps (reduced value) + IC products below 2^64 between reductions
   const int O = 2 * c.Kp;
   // no wider group block than the groups present
@@ -485,19 +500,26 @@ static cudaError_t run_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, con
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(c.n / 32, c.L, (G + GC - 1) / GC);
-  k_mac_tiled<GT, OT><<<grid, warps * 32, smem, st>>>(c, pt, model, acc, G, GC, IC);
+  k_mac_tiled<GT, OT><<<grid, warps * 32, smem, st>>>(c, pt, model, acc, G, GC, IC, pP, mi0,
+                                                       cnt, accum);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
-                             uint32_t* acc, const MacTiling& t, cudaStream_t st) {
+                             uint32_t* acc, const MacTiling& t, cudaStream_t st, int pP, int mi0,
+                             int cnt, int accum) {
+  if (pP <= 0) pP = cnt = (int)c.P;  // the whole pass
   switch (t.gt * 100 + t.ot) {
-    case 204: return run_mac_tiled<2, 4>(c, pt, G, model, acc, t.gc, t.ic, st);
-    case 207: return run_mac_tiled<2, 7>(c, pt, G, model, acc, t.gc, t.ic, st);
-    case 208: return run_mac_tiled<2, 8>(c, pt, G, model, acc, t.gc, t.ic, st);
-    case 404: return run_mac_tiled<4, 4>(c, pt, G, model, acc, t.gc, t.ic, st);
-    case 407: return run_mac_tiled<4, 7>(c, pt, G, model, acc, t.gc, t.ic, st);
-    case 408: return run_mac_tiled<4, 8>(c, pt, G, model, acc, t.gc, t.ic, st);
+#define EPHDC_TILED(GT_, OT_)                                                              \
+  case GT_ * 100 + OT_:                                                                    \
+    return run_mac_tiled<GT_, OT_>(c, pt, G, model, acc, t.gc, t.ic, pP, mi0, cnt, accum, st);
+    EPHDC_TILED(2, 4)
+    EPHDC_TILED(2, 7)
+    EPHDC_TILED(2, 8)
+    EPHDC_TILED(4, 4)
+    EPHDC_TILED(4, 7)
+    EPHDC_TILED(4, 8)
+#undef EPHDC_TILED
     default: return cudaErrorInvalidConfiguration;
   }
 }

@@ -84,5 +84,13 @@ def test_face1024_throughput_step_every_tiled_schedule():
     # (4 groups and 4 outputs per warp, 32 groups per CTA, 15 plaintexts per chunk)
     AT.apply(ctx, {"mac_mode": 2, "mac_tile": 4043215})
     _check_groups(ctx, w, ctx.infer(X, Wt, model, gk), digests)
+    # the pass in plaintext-index chunks (encode a chunk of every group, accumulate it,
+    # next chunk): the same ciphertexts, with a ragged last chunk (1250 = 52 x 24 + 2)
+    for chunk in (24, 125):
+        ctx.tune_set("chunk", chunk)
+        got = ctx.infer(X, Wt, model, gk)
+        ctx.device_status()
+        assert torch.equal(got, ref), chunk
+    ctx.tune_set("chunk", 0)
     for cx in ctxs:
         cx.close()
