@@ -842,16 +842,22 @@ def run_legs(args):
     import torch
     from paper_2511_00737_gb300 import workload as WL
     out = {}
-    for name, steps in (("clients64", 50), ("serve", 0), ("dense65536", 5)):
+    # (leg, workload, steps, plaintext chunk): the last leg times the headline step as a
+    # chunked pass (96 plaintext indices of every group encoded and accumulated at a
+    # time), the measured answer to whether keeping each chunk's plaintexts in L2 pays
+    legs = (("clients64", "clients64", 50, 0), ("serve", "serve", 0, 0),
+            ("dense65536", "dense65536", 5, 0), ("face1024_chunked96", "face1024", 100, 96))
+    for name, wname, steps, chunk in legs:
         a = copy.copy(args)
-        a.workload = name
+        a.workload = wname
         a.steps = max(1, min(args.steps, steps))
         a.warmup = 3
         a.no_cpu_baseline = a.no_perquery = a.no_sr = True
         a.pack, a.mac_mode, a.mac_tile, a.hdc_mode = 0, -1, -1, -1
-        w = WL.config(name)
+        a.chunk = chunk
+        w = WL.config(wname)
         t0 = time.perf_counter()
-        line = run_serve(a, w) if name == "serve" else run_ours(a, w, w.B)
+        line = run_serve(a, w) if wname == "serve" else run_ours(a, w, w.B)
         rec = {k: line[k] for k in LEG_KEYS if k in line}
         rec["wall_s"] = time.perf_counter() - t0
         if name == "serve":
