@@ -349,8 +349,11 @@ struct PaddedAccess<F, decltype((void)F::kPadded)> {
 
 // FINAL: forward -> reduce outputs to [0, p); inverse -> multiply by n^-1, reduce
 // NSCALE = false: the inverse's final pass only reduces (its input was scaled by n^-1)
+// FERMAT (inverse mod t = 2^16 + 1 only): values stay in [0, t) and the twiddle
+// product d w (d <= 2^16, w < 2^16: below 2^32) is reduced without a multiply, as
+// 2^16 = -1 (mod t) gives d w = lo + 2^16 hi = lo - hi (mod t)
 template <int LOGN, int K, int LOGM0, bool FWD, bool FINAL, class LD, class ST,
-          bool NSCALE = true>
+          bool NSCALE = true, bool FERMAT = false>
 __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP& m, LD ld, ST st) {
   constexpr int LOGS = LOGN - LOGM0 - K;
   constexpr uint32_t S = 1u << LOGS;
@@ -399,6 +402,14 @@ __device__ __forceinline__ void pass_t(const uint2* __restrict__ tw, const ModP&
           const uint32_t T = mulshoup(x[e + half], ww.x, ww.y, p);
           x[e] = X + T;
           x[e + half] = X - T + two_p;
+        } else if (FERMAT) {
+          const uint32_t X = x[e], Y = x[e + half];
+          const uint32_t U = X + Y, D0 = X - Y + p;  // p = t here; both in [0, 2t)
+          x[e] = min(U, U - p);
+          const uint32_t D = min(D0, D0 - p);        // [0, t)
+          const uint32_t P = D * ww.x;               // < 2^16 (2^16 - 1) < 2^32
+          const uint32_t R = (P & 0xFFFFu) + p - (P >> 16);  // [1, 2t)
+          x[e + half] = min(R, R - p);
         } else {
           const uint32_t X = x[e], Y = x[e + half];
           const uint32_t U = X + Y;
@@ -450,23 +461,27 @@ __device__ __forceinline__ void fwd_passes(uint32_t* s, const ModP& m, LD ld, ST
     fwd_passes<LOGN, I + 1, LD, ST, V>(s, m, ld, st);
   }
 }
-template <int LOGN, int I, class LD, class ST, int V = 0, bool NSCALE = true>
+template <int LOGN, int I, class LD, class ST, int V = 0, bool NSCALE = true,
+          bool FERMAT = false>
 __device__ __forceinline__ void inv_passes(uint32_t* s, const ModP& m, LD ld, ST st) {
   using Pl = NttPlan<LOGN, V>;
   if constexpr (I >= 0) {
     constexpr bool first = I == Pl::NP - 1, last = I == 0;
     if constexpr (first && last) {
-      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true, LD, ST, NSCALE>(m.itw, m, ld, st);
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true, LD, ST, NSCALE, FERMAT>(m.itw, m, ld,
+                                                                                 st);
     } else if constexpr (first) {
-      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, ld, SmemSt{s});
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false, LD, SmemSt, true, FERMAT>(
+          m.itw, m, ld, SmemSt{s});
     } else if constexpr (last) {
-      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true, SmemLd, ST, NSCALE>(m.itw, m, SmemLd{s},
-                                                                             st);
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, true, SmemLd, ST, NSCALE, FERMAT>(
+          m.itw, m, SmemLd{s}, st);
     } else {
-      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false>(m.itw, m, SmemLd{s}, SmemSt{s});
+      pass_t<LOGN, Pl::K(I), Pl::LOGM0(I), false, false, SmemLd, SmemSt, true, FERMAT>(
+          m.itw, m, SmemLd{s}, SmemSt{s});
     }
     __syncthreads();
-    inv_passes<LOGN, I - 1, LD, ST, V, NSCALE>(s, m, ld, st);
+    inv_passes<LOGN, I - 1, LD, ST, V, NSCALE, FERMAT>(s, m, ld, st);
   }
 }
 // Forward NTT: `ld(i)` supplies natural-order input i (values in [0, 4p)) to the first
@@ -478,18 +493,18 @@ __device__ __forceinline__ void ntt_fwd_io(uint32_t* s, const ModP& m, LD ld, ST
 }
 // Inverse NTT: device-order input (values in [0, 2p)) in, natural-order output in
 // [0, p) out.  Ends with a barrier.
-template <int LOGN, class LD, class ST, int V = 0, bool NSCALE = true>
+template <int LOGN, class LD, class ST, int V = 0, bool NSCALE = true, bool FERMAT = false>
 __device__ __forceinline__ void ntt_inv_io(uint32_t* s, const ModP& m, LD ld, ST st) {
-  inv_passes<LOGN, NttPlan<LOGN, V>::NP - 1, LD, ST, V, NSCALE>(s, m, ld, st);
+  inv_passes<LOGN, NttPlan<LOGN, V>::NP - 1, LD, ST, V, NSCALE, FERMAT>(s, m, ld, st);
 }
 // in-place variants on the padded shared buffer
 template <int LOGN, int V = 0>
 __device__ __forceinline__ void ntt_fwd_t(uint32_t* s, const ModP& m) {
   ntt_fwd_io<LOGN, SmemLd, SmemSt, V>(s, m, SmemLd{s}, SmemSt{s});
 }
-template <int LOGN, int V = 0, bool NSCALE = true>
+template <int LOGN, int V = 0, bool NSCALE = true, bool FERMAT = false>
 __device__ __forceinline__ void ntt_inv_t(uint32_t* s, const ModP& m) {
-  ntt_inv_io<LOGN, SmemLd, SmemSt, V, NSCALE>(s, m, SmemLd{s}, SmemSt{s});
+  ntt_inv_io<LOGN, SmemLd, SmemSt, V, NSCALE, FERMAT>(s, m, SmemLd{s}, SmemSt{s});
 }
 
 // dispatch a kernel template on log2(n) (n = 1024 .. 16384)

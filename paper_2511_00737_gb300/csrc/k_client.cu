@@ -59,7 +59,10 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
   }
   pack_query_slots(c, H, B, g, i, mb);
   __syncthreads();
-  ntt_inv_t<LOGN, V, false>(mb, c.mt);  // slots (scaled by n^-1) -> coefficients in [0, t)
+  // slots (scaled by n^-1) -> coefficients in [0, t); t = 2^16 + 1 without multiplies
+  // in the reductions
+  if (c.t == 65537u) ntt_inv_t<LOGN, V, false, true>(mb, c.mt);
+  else ntt_inv_t<LOGN, V, false>(mb, c.mt);
   const uint32_t t = c.t, thalf = (t - 1) / 2;
   for (uint32_t l = 0; l < c.L; l++) {
     const ModP m = c.mq[l];
