@@ -291,7 +291,24 @@ def run_ours(args, w, B):
         out = pipe.out
         enc, _, _ = AT.tune_encode(ctx, ctx.hdc_encode(torch.cat(Xd[0]), Wt), reps=3)
         tuned = {**tuned, **enc}
-        step = lambda i: pipe.run(Xd[i % R])
+        # consecutive steps alternate over S pipelines (each its own context, graphs and
+        # stream, sharing the model and keys), so one step's MAC and rotations overlap
+        # the next step's encoding
+        S = max(1, args.streams)
+        ctxs = [ctx] + [E.Context.for_workload(w, max_batch=ctx.groups(B) * cap)
+                        for _ in range(S - 1)]
+        for cx in ctxs[1:]:
+            cx.tune_set("layout", layout)
+            AT.apply(cx, tuned)
+        pipes = [pipe] + [BT.GraphedPipeline(cx, Wt, model, gk, max_groups=ctx.groups(B))
+                          for cx in ctxs[1:]]
+        for p_ in pipes:
+            p_.graph(ctx.groups(B))   # captured before timing
+        streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
+        outs = [p_.out for p_ in pipes]
+
+        def step(i):
+            pipes[i % S].launch(Xd[i % R], streams[i % S])
     else:
         Xh = [torch.from_numpy(WL.features(seed, B, w.F, batch=b)).pin_memory() for b in range(R)]
         Xd = [x.to(dev) for x in Xh]
@@ -353,8 +370,8 @@ def run_ours(args, w, B):
     barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    all_ctx = [ctx] if multi else ctxs
-    side = [] if multi else streams
+    all_ctx = ctxs
+    side = streams
     for cx in all_ctx:
         cx.profile(True)
         cx.profile_read()
@@ -404,18 +421,19 @@ def run_ours(args, w, B):
         roof_pass = "a single-stream pass of %d steps after the timed region" % k1
     if multi:
         # graph replays record no stage events: take the stage breakdown and the
-        # launches per step from a few eager steps of the same packed work
-        pipe.use_graphs = False
-        ctx.profile_read()
+        # launches per step from a few eager steps of the same packed work on one stream
+        read_stages()
         ksteps_eager = 5
+        pipe.use_graphs = False
         for i in range(ksteps_eager):
-            step(i)
+            pipe.launch(Xd[i % R], streams[0])
         torch.cuda.synchronize()
-        stage_ms, stage_calls, launches = ctx.profile_read()
+        stage_ms, stage_calls, launches = read_stages()
         stage_ms = {k: v * args.steps / ksteps_eager for k, v in stage_ms.items()}
         stage_calls = {k: v * args.steps // ksteps_eager for k, v in stage_calls.items()}
         launches = launches * args.steps // ksteps_eager
         pipe.use_graphs = True
+        roof_pass = "%d eager single-stream steps after the timed region" % ksteps_eager
         if can_check:
             res, _ = pipe.run(Xd[0])   # the timed step's graph on feature set 0
             torch.cuda.synchronize()
@@ -428,8 +446,7 @@ def run_ours(args, w, B):
 
     # end to end: pinned host inputs in, score ciphertexts back to pinned host
     ksteps = max(1, min(args.steps, 300))
-    out_hs = [out_h] if multi else [out_h] + [
-        torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs[1:]]
+    out_hs = [out_h] + [torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs[1:]]
     barrier()
     torch.cuda.synchronize()
     e0.record(st)
@@ -437,10 +454,12 @@ def run_ours(args, w, B):
         s_.wait_stream(st)
     for i in range(ksteps):
         if multi:
-            for xd, xh in zip(Xd[i % R], Xh[i % R]):
-                xd.copy_(xh, non_blocking=True)
-            step(i)
-            out_h.copy_(out, non_blocking=True)
+            j = i % S
+            with torch.cuda.stream(streams[j]):
+                for xd, xh in zip(Xd[i % R], Xh[i % R]):
+                    xd.copy_(xh, non_blocking=True)
+                res, _ = pipes[j].launch(Xd[i % R], streams[j])
+                out_hs[j][:res.numel()].copy_(res, non_blocking=True)
         else:
             j = i % S
             with torch.cuda.stream(streams[j]):
@@ -504,10 +523,11 @@ def run_ours(args, w, B):
         if not multi and tuned:
             line["config"]["mac_schedule"] = tuned
         if multi:
+            line["config"]["streams"] = S
             line["config"]["clients"] = len(w.clients)
             line["config"]["mac_schedule"] = tuned
             line["config"]["cuda_graph"] = True
-    for cx in ([ctx] if multi else ctxs):
+    for cx in ctxs:
         cx.close()
     if dist is not None:
         dist.destroy_process_group()

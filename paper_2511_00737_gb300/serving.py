@@ -201,16 +201,25 @@ class Server:
             s.warm()
 
     # ------------------------------------------------------------------ events
-    def arrive(self, req, now):
+    def arrive(self, req, now, admit=True):
+        """A request arrives; with admit=False the caller admits a whole batch of
+        arrivals at once afterwards (one upload event for all of them)."""
         req.nbytes = self.request_bytes(req.B)
         if req.nbytes > self.budget or req.B > self.max_queries:
             req.done = now
             self.rejected.append(req)
             return
         self.pending.append(req)
+        if admit:
+            self._admit(now)
+            if self.pending and self.pending[-1] is req:
+                self.waited += 1   # no free range on arrival: it waits for memory
+
+    def admit_arrivals(self, reqs, now):
+        """Admits what fits of a batch of requests that arrived together (see arrive)."""
         self._admit(now)
-        if self.pending and self.pending[-1] is req:
-            self.waited += 1   # no free range on arrival: it waits for memory
+        waiting = {id(r) for r in self.pending}
+        self.waited += sum(1 for r in reqs if id(r) in waiting)
 
     def _admit(self, now):
         placed = []
@@ -329,10 +338,14 @@ class Server:
         nxt = 0
         while True:
             now = time.perf_counter() - t0
+            due = []
             while nxt < len(order) and arrivals[order[nxt]] * time_scale <= now:
                 rid = int(order[nxt])
-                self.arrive(Request(rid, arrivals[rid] * time_scale, make_X(rid)), now)
+                due.append(Request(rid, arrivals[rid] * time_scale, make_X(rid)))
+                self.arrive(due[-1], now, admit=False)
                 nxt += 1
+            if due:
+                self.admit_arrivals(due, now)
             busy = self.poll(time.perf_counter() - t0)
             if nxt >= len(order) and not busy:
                 break

@@ -110,6 +110,38 @@ def test_graph_replay_equals_eager_and_is_reused():
     ctx.close()
 
 
+def test_pipelines_on_several_streams_give_the_same_ciphertexts():
+    """Consecutive packed steps alternating over three pipelines (each its own context,
+    graphs and stream, all sharing the model and keys), launched without any
+    synchronisation between them, give each step the ciphertexts of running it alone."""
+    w, ctx, Xs, Wt, cls, sk, gk, model = _setup(SIZES, max_batch=4 * 256)
+    Wd = _dev(Wt)
+    ctxs = [ctx] + [E.Context(w.n, w.L, w.k, w.k_in, w.r, w.D, w.F, w.bits, w.shift, 4 * 256)
+                    for _ in range(2)]
+    pipes = [BT.GraphedPipeline(cx, Wd, model, gk, max_groups=4) for cx in ctxs]
+    streams = [torch.cuda.Stream() for _ in ctxs]
+    mixes = [Xs, Xs[::-1], [Xs[2], Xs[6]], [Xs[2]], Xs[1:], [Xs[4]]]
+    dmixes = [[_dev(x) for x in mix] for mix in mixes]
+    alone = []
+    for dmix in dmixes:
+        out, _ = pipes[0].run(dmix)
+        torch.cuda.synchronize()
+        alone.append(out.clone())
+    torch.cuda.synchronize()
+    got = []
+    for i, dmix in enumerate(dmixes):    # no synchronisation between the steps
+        j = i % 3
+        out, _ = pipes[j].launch(dmix, streams[j])
+        with torch.cuda.stream(streams[j]):
+            got.append(out.clone())      # before this pipeline's next step overwrites it
+    torch.cuda.synchronize()
+    for i, out in enumerate(got):
+        assert torch.equal(out, alone[i]), i
+    for cx in ctxs[1:]:
+        cx.close()
+    ctx.close()
+
+
 def test_autotuner_picks_a_schedule_and_results_do_not_change(tmp_path, monkeypatch):
     monkeypatch.setattr(AT, "CACHE", str(tmp_path / "tune.json"))
     sizes = [600, 600, 600]
