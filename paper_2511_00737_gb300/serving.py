@@ -230,31 +230,30 @@ class Server:
                 break
             self.pending.popleft()
             r.off, r.admitted = off, now
-            self._place(r)
             placed.append(r)
             self.queue.append(r)
         if placed and self.arena.buf is not None:
-            # one event after the copies of everything admitted together
+            self._place(placed)
+
+    def _place(self, reqs):
+        """Copies admitted requests' features into their arena ranges on the upload
+        stream, after the work already on the caller's current stream (which may be
+        producing them); each request then holds its arena view and one event recorded
+        after all of the copies."""
+        # ordered after the caller's stream once for the whole batch
+        self.upload.wait_stream(torch.cuda.current_stream(self.arena.buf.device))
+        with torch.cuda.stream(self.upload):
+            for r in reqs:
+                src = r.X if isinstance(r.X, torch.Tensor) else torch.from_numpy(np.asarray(r.X))
+                dst = self.arena.view(r.off, r.B, self.w.F)
+                dst.copy_(src, non_blocking=True)
+                if src.is_cuda:
+                    src.record_stream(self.upload)   # the caller may free X after this
+                r.X = dst
             ev = torch.cuda.Event()
             ev.record(self.upload)
-            for r in placed:
-                r.ready = ev
-
-    def _place(self, r):
-        """Copies an admitted request's features into its arena range on the upload
-        stream, after the work already on the caller's current stream (which may be
-        producing them); the request then holds the arena view."""
-        if self.arena.buf is None:
-            return
-        src = r.X if isinstance(r.X, torch.Tensor) else torch.from_numpy(np.asarray(r.X))
-        dst = self.arena.view(r.off, r.B, self.w.F)
-        if src.is_cuda:
-            self.upload.wait_stream(torch.cuda.current_stream(src.device))
-        with torch.cuda.stream(self.upload):
-            dst.copy_(src, non_blocking=True)
-        if src.is_cuda:
-            src.record_stream(self.upload)   # the caller may free X once this returns
-        r.X = dst
+        for r in reqs:
+            r.ready = ev
 
     def _free(self, r):
         if r.off is not None:
