@@ -273,7 +273,7 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
 
 /* Schedule knobs of the multi-accumulate (set by the autotuner; results never
  * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled / 3 tensor cores (exact
- * byte split, k/k_in <= 16), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
+ * signed-digit split, k/k_in <= 16), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
  * cores from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
  * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
  * warp, groups per CTA, plaintexts per staged chunk, at most 15); "hdc_mode" 0..3 is
@@ -290,8 +290,12 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * encrypted under.  With layout 1 the multiply-accumulate always runs on the tensor
  * cores ("mac_mode" 1 or 2 fails with EPHDC_EUNSUPPORTED), and the seeded model message,
  * the server-side variant, the noise-growth trial and bfv_ptct_similarity_noalloc
- * return EPHDC_EUNSUPPORTED.  EPHDC_EINVAL for an unknown knob or an invalid value.
- * ephdc_tune_get returns -1 for an unknown knob. */
+ * return EPHDC_EUNSUPPORTED.  "chunk" c > 0 makes ephdc_infer, when it runs the tiled
+ * multi-accumulate with layout 0 and no scaling operation, encode and accumulate
+ * plaintext indices [i0, i0 + c) of every group at a time in the plaintext scratch
+ * instead of the whole pass (same results; measured slower on GB300); 0 = off.
+ * EPHDC_EINVAL for an unknown knob or an invalid value.  ephdc_tune_get returns -1 for
+ * an unknown knob. */
 ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);
 int64_t ephdc_tune_get(const ephdc_ctx* ctx, const char* knob);
 
