@@ -829,8 +829,9 @@ ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_
                                           G < c->mac_tc_min_groups);
   if (c->chunk > 0 && (uint32_t)c->chunk < d.P && tiled && !d.layout && !d.scale_g) {
     // plaintext-index chunks: each chunk's plaintexts of all G groups are encoded into
-    // the start of the plaintext buffer and accumulated from there while they are
-    // still in L2 (the whole pass writes and reads every plaintext through HBM once)
+    // the start of the plaintext buffer and accumulated from there, so that they could
+    // be read back from L2 rather than HBM (on GB300 they still come from DRAM and the
+    // chunked pass is slower than the whole pass)
     for (uint32_t i0 = 0; i0 < d.P && e == cudaSuccess; i0 += (uint32_t)c->chunk) {
       const uint32_t ni = d.P - i0 < (uint32_t)c->chunk ? d.P - i0 : (uint32_t)c->chunk;
       {
