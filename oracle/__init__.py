@@ -61,6 +61,8 @@ def lib():
             "or_fold_galois": (u32, [vp, u32]),
             "or_keygen": (None, [vp, u64, vp, vp]),
             "or_encrypt_model": (None, [vp, u64, vp, vp, vp]),
+            "or_encrypt_model_seeded_ntt": (None, [vp, u64, vp, vp, vp]),
+            "or_seeded_ntt_c1": (None, [vp, u64, u64, vp]),
             "or_hdc_encode": (None, [vp, vp, i32, u32, u32, i32, u32, vp]),
             "or_encode_plain": (None, [vp, vp, i32, vp]),
             "or_ptct_mac": (None, [vp, vp, i32, vp, vp]),
@@ -282,6 +284,22 @@ class Oracle:
         lib().or_encrypt_model(self.ctx, seed, _p(classes), _p(np.ascontiguousarray(s, np.int32)),
                                _p(model))
         return model
+
+    def encrypt_model_seeded_ntt(self, seed, classes, s):
+        """The compact model whose c1 is regenerated in the evaluation domain (domain 8,
+        word l*n + brv(j) at evaluation psi^(2j+1)); the whole model in the coefficient
+        domain, like encrypt_model."""
+        classes = np.ascontiguousarray(classes, np.int8)
+        assert classes.shape == (self.k, self.D)
+        model = np.zeros((self.P, self.Kp, 2, self.L, self.n), np.uint32)
+        lib().or_encrypt_model_seeded_ntt(self.ctx, seed, _p(classes),
+                                          _p(np.ascontiguousarray(s, np.int32)), _p(model))
+        return model
+
+    def seeded_ntt_c1(self, seed, cidx):
+        a = np.zeros((self.L, self.n), np.uint32)
+        lib().or_seeded_ntt_c1(self.ctx, seed, cidx, _p(a))
+        return a
 
     def encrypt_slots(self, seed, obj, s, slots):
         ct = np.zeros((2, self.L, self.n), np.uint32)

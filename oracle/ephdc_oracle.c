@@ -648,6 +648,69 @@ void or_encrypt_model(const or_ctx* c, u64 seed, const int8_t* classes, const i3
   }
 }
 
+/* The compact model of Sec. 4.1 (the model shipped once): only c0 travels and c1 is
+ * regenerated from the seed, here directly in the evaluation domain so that a client
+ * can regenerate it while it multiplies.  Convention: c1 of model ciphertext cidx in
+ * limb l, evaluated at psi_l^(2j+1), is word64(l*n + brv(j)) mod q_l of the stream
+ * (seed, domain 8, cidx), brv reversing the log2 n bits of j (position brv(j) of the
+ * evaluation order in which a bit-reversed transform leaves it).  c0 follows the same
+ * rule as or_encrypt_model with that c1.  Output: the whole model in the coefficient
+ * domain, [P][k/k_in][2][L][n]. */
+static u32 bit_reverse(u32 v, u32 bits) {
+  u32 r = 0;
+  for (u32 b = 0; b < bits; b++) r |= ((v >> b) & 1u) << (bits - 1 - b);
+  return r;
+}
+
+void or_seeded_ntt_c1(const or_ctx* c, u64 seed, u64 cidx, u32* a_out) {
+  u32 n = c->n, logn = 0;
+  while ((1u << logn) < n) logn++;
+  stream_t s;
+  stream_init(&s, seed, 8, cidx);
+  for (u32 l = 0; l < c->L; l++) {
+    u32* a = a_out + (u64)l * n;
+    for (u32 j = 0; j < n; j++)
+      a[j] = (u32)(stream_word64(&s, (u64)l * n + bit_reverse(j, logn)) % c->q[l]);
+    or_intt(n, c->q[l], c->psi[l], a);  /* evaluations -> coefficients */
+  }
+}
+
+void or_encrypt_model_seeded_ntt(const or_ctx* c, u64 seed, const int8_t* classes, const i32* s,
+                                 u32* model) {
+  u32 n = c->n, L = c->L;
+#pragma omp parallel
+  {
+    u32* slots = (u32*)malloc(sizeof(u32) * n);
+    u32* m = (u32*)malloc(sizeof(u32) * n);
+    u32* a = (u32*)malloc(sizeof(u32) * L * n);
+    i32* e = (i32*)malloc(sizeof(i32) * n);
+    u32* sl = (u32*)malloc(sizeof(u32) * n);
+    u32* as = (u32*)malloc(sizeof(u32) * n);
+#pragma omp for schedule(dynamic)
+    for (i64 cidx = 0; cidx < (i64)c->P * c->Kp; cidx++) {
+      u32 i = (u32)(cidx / c->Kp), jp = (u32)(cidx % c->Kp);
+      class_slots(c, classes, i, jp, slots);
+      or_slot_encode(n, c->t, c->zeta, slots, m);
+      or_seeded_ntt_c1(c, seed, (u64)cidx, a);
+      or_sample_gauss(seed, 3, (u64)cidx, n, c->cdt, e);
+      for (u32 l = 0; l < L; l++) {
+        u32 p = c->q[l];
+        for (u32 kk = 0; kk < n; kk++) sl[kk] = smod(s[kk], p);
+        or_polymul(n, p, c->psi[l], a + (u64)l * n, sl, as);
+        u32* c0 = model + (((u64)cidx * 2 + 0) * L + l) * n;
+        u32* c1 = model + (((u64)cidx * 2 + 1) * L + l) * n;
+        for (u32 kk = 0; kk < n; kk++) {
+          u32 v = submod(smod(e[kk], p), as[kk], p);
+          v = addmod(v, scaled_msg(c, l, m[kk]), p);
+          c0[kk] = v;
+          c1[kk] = a[(u64)l * n + kk];
+        }
+      }
+    }
+    free(slots); free(m); free(a); free(e); free(sl); free(as);
+  }
+}
+
 /* ------------------------------------------------------------------------- */
 /* HDC encoding (Sec. 2.1 random projection) and quantisation (Sec. 5.1)       */
 /* ------------------------------------------------------------------------- */
