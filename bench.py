@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0,
                     help="encode and accumulate this many plaintext indices of every group "
                          "at a time (0 = the whole pass at once)")
+    ap.add_argument("--compact", action="store_true",
+                    help="the compact model: c0 stored, c1 regenerated by the tiled MAC")
     ap.add_argument("--no-legs", action="store_true",
                     help="time only the headline workload (not clients64, serve, dense65536)")
     return ap.parse_args()
@@ -267,6 +269,9 @@ def run_ours(args, w, B):
     # 16-byte stores)
     layout = max(0, args.layout)
     ctx.tune_set("layout", layout)
+    # the compact model: only c0 stored, c1 regenerated by the multiply-accumulate
+    model_seed = seed if args.compact else -1
+    ctx.tune_set("model_seed", model_seed)
     if args.mac_mode >= 0:
         ctx.tune_set("mac_mode", args.mac_mode)
     if args.hdc_mode >= 0:
@@ -299,6 +304,7 @@ def run_ours(args, w, B):
                         for _ in range(S - 1)]
         for cx in ctxs[1:]:
             cx.tune_set("layout", layout)
+            cx.tune_set("model_seed", model_seed)
             AT.apply(cx, tuned)
         pipes = [pipe] + [BT.GraphedPipeline(cx, Wt, model, gk, max_groups=ctx.groups(B))
                           for cx in ctxs[1:]]
@@ -332,7 +338,8 @@ def run_ours(args, w, B):
         S = max(1, args.streams)
         ctxs = [ctx] + [E.Context.for_workload(w, max_batch=B) for _ in range(S - 1)]
         for cx in ctxs[1:]:
-            cx.tune_set("layout", layout)  # the shared model's layout
+            cx.tune_set("layout", layout)  # the shared model's layout and form
+            cx.tune_set("model_seed", model_seed)
             if tuned:
                 AT.apply(cx, tuned)
         for cx in ctxs:
@@ -401,6 +408,7 @@ def run_ours(args, w, B):
     # last % R; with the digests' inputs (set 0 of the rank-0 seed) check it
     parity = None
     can_check = (rank == 0 and not args.dim and not args.batch and w.name in DIGESTS and
+                 not args.compact and
                  (multi or (w.name != "face1024" or (batch == 1024 and pack == 16))))
     if can_check and not multi:
         last = max(i for i in range(args.steps) if i % S == 0)
@@ -520,6 +528,9 @@ def run_ours(args, w, B):
             line["config"]["batches_per_step"] = pack
             line["config"]["batch"] = batch
         line["config"]["storage_layout"] = "coefficient-blocked" if layout else "standard"
+        if args.compact:
+            line["config"]["model"] = ("compact: c0 stored, c1 regenerated from the seed by "
+                                       "the multiply-accumulate")
         if not multi and tuned:
             line["config"]["mac_schedule"] = tuned
         if multi:
@@ -866,7 +877,8 @@ def run_legs(args):
     # chunked pass (96 plaintext indices of every group encoded and accumulated at a
     # time), the measured answer to whether keeping each chunk's plaintexts in L2 pays
     legs = (("clients64", "clients64", 50, 0), ("serve", "serve", 0, 0),
-            ("dense65536", "dense65536", 5, 0), ("face1024_chunked96", "face1024", 100, 96))
+            ("dense65536", "dense65536", 5, 0), ("face1024_chunked96", "face1024", 100, 96),
+            ("face1024_compact_model", "face1024", 100, -1))
     for name, wname, steps, chunk in legs:
         a = copy.copy(args)
         a.workload = wname
@@ -874,7 +886,8 @@ def run_legs(args):
         a.warmup = 3
         a.no_cpu_baseline = a.no_perquery = a.no_sr = True
         a.pack, a.mac_mode, a.mac_tile, a.hdc_mode = 0, -1, -1, -1
-        a.chunk = chunk
+        a.chunk = max(0, chunk)
+        a.compact = chunk < 0   # the compact-model leg
         w = WL.config(wname)
         t0 = time.perf_counter()
         line = run_serve(a, w) if wname == "serve" else run_ours(a, w, w.B)

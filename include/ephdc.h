@@ -294,6 +294,15 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * multi-accumulate with layout 0 and no scaling operation, encode and accumulate
  * plaintext indices [i0, i0 + c) of every group at a time in the plaintext scratch
  * instead of the whole pass (same results; measured slower on GB300); 0 = off.
+ * "model_seed" s >= 0 selects the compact model (Sec. 4.1: the model is shipped once;
+ * here only c0 is ever stored, ephdc_model_bytes halves): bfv_encrypt_model draws c1 in
+ * the evaluation domain, device position k of limb l = word64(l n + k) mod q_l of the
+ * ChaCha20 stream (s, domain 8, ciphertext number), and stores c0 only, [P][k/k_in][L][n];
+ * the tiled multiply-accumulate regenerates c1 from s as it stages the model (the
+ * automatic and the tiled "mac_mode" only).  -1 (the default) = the full model.  Set it,
+ * with the seed the model is encrypted with, on every context that uses the model and
+ * before bfv_encrypt_model; the blocked layout, the seeded model message, the noise-growth
+ * trial and bfv_ptct_similarity_noalloc do not take it (EPHDC_EUNSUPPORTED).
  * EPHDC_EINVAL for an unknown knob or an invalid value.  ephdc_tune_get returns -1 for
  * an unknown knob. */
 ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);

@@ -20,8 +20,9 @@ CACHE = os.environ.get("EPHDC_TUNE_CACHE",
 
 def _key(ctx, G):
     name = torch.cuda.get_device_name(ctx.device).replace(" ", "_")
-    return "%s|n%d|L%d|k%d|kin%d|r%d|G%d|lay%d" % (name, ctx.n, ctx.L, ctx.k, ctx.k_in, ctx.r, G,
-                                                  ctx.tune_get("layout"))
+    return "%s|n%d|L%d|k%d|kin%d|r%d|G%d|lay%d|cm%d" % (
+        name, ctx.n, ctx.L, ctx.k, ctx.k_in, ctx.r, G, ctx.tune_get("layout"),
+        int(ctx.tune_get("model_seed") >= 0))
 
 
 def _load():
@@ -43,8 +44,11 @@ def candidates(ctx, G):
     O = 2 * ctx.Kp
     if ctx.tune_get("layout") == 1:
         return [{"mac_mode": 3}]   # the blocked layout is read by the tensor cores only
-    out = [{"mac_mode": 1, "mac_splits": s} for s in (0, 8, 16, 32)]
-    if G >= 2 and O <= 32:
+    compact = ctx.tune_get("model_seed") >= 0  # regenerated by the tiled kernel only
+    if compact and G < 2:
+        return [{"mac_mode": 2}]
+    out = [] if compact else [{"mac_mode": 1, "mac_splits": s} for s in (0, 8, 16, 32)]
+    if G >= 2 and O <= 32 and not compact:
         out.append({"mac_mode": 3})
     if G >= 2:
         for gt in (2, 4):

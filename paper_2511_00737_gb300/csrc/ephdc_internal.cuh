@@ -70,6 +70,12 @@ struct DevCtx {
   // every (group, plaintext) and (plaintext, output) pair are 16 contiguous bytes and a
   // block's pairs are contiguous (read by the tensor-core multiply-accumulate)
   uint32_t layout;
+  // compact model (Sec. 4.1, the model shipped once): only c0 is stored, [P][O/2][L][n],
+  // and c1 at device position k of limb l is word64(l n + k) mod q_l of the ChaCha20
+  // stream (model_seed, domain 8, ciphertext number), regenerated by the tiled
+  // multiply-accumulate as it reads the model
+  uint32_t compact;
+  uint64_t model_seed;
 };
 
 // word index of coefficient k of limb l of pair (a, b) in the blocked layout
@@ -755,6 +761,8 @@ cudaError_t launch_ntt_natural(const DevCtx& c, uint32_t limb, uint32_t* poly, i
                                int inverse, cudaStream_t st);
 cudaError_t launch_unblock(const DevCtx& c, const uint32_t* src, uint32_t* dst, uint32_t A,
                            uint32_t B, cudaStream_t st);
+cudaError_t launch_expand_compact(const DevCtx& c, const uint32_t* c0, uint32_t* full,
+                                  cudaStream_t st);
 cudaError_t launch_to_coeff(const DevCtx& c, const uint32_t* in, uint32_t* out, int count,
                             int limbs_per_item, int in_stride_words, int limb_stride_words,
                             int limb0_is_digit_major, cudaStream_t st);

@@ -515,7 +515,9 @@ size_t ephdc_galois_key_bytes(const ephdc_ctx* c) {
   return c ? (size_t)c->dc.logr * c->dc.L * c->dc.L * 4 * c->dc.n * sizeof(uint32_t) : 0;
 }
 size_t ephdc_model_bytes(const ephdc_ctx* c) {
-  return c ? (size_t)c->dc.P * c->dc.Kp * 2 * c->dc.L * c->dc.n * sizeof(uint32_t) : 0;
+  return c ? (size_t)c->dc.P * c->dc.Kp * (c->dc.compact ? 1 : 2) * c->dc.L * c->dc.n *
+                 sizeof(uint32_t)
+           : 0;
 }
 size_t ephdc_plain_bytes(const ephdc_ctx* c, int32_t B) {
   if (!c || B < 1) return 0;
@@ -574,12 +576,17 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
   cudaError_t e;
   {
     const bool tc_ok = 2 * d.Kp <= 32 && d.P < 16384;
-    // the blocked layout is read by the tensor-core product only
+    // the blocked layout is read by the tensor-core product only, the compact model by
+    // the tiled product only (it regenerates c1 while staging the model)
     if (d.layout && (c->mac_mode == 1 || c->mac_mode == 2))
       return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs mac_mode 0 or 3");
-    const bool tc = tc_ok && (c->mac_mode == 3 || d.layout ||
-                              (c->mac_mode == 0 && G >= c->mac_tc_min_groups));
-    const bool tiled = !tc && (c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups));
+    if (d.compact && (c->mac_mode == 1 || c->mac_mode == 3))
+      return fail(c, EPHDC_EUNSUPPORTED, "the compact model needs mac_mode 0 or 2");
+    const bool tc = !d.compact && tc_ok &&
+                    (c->mac_mode == 3 || d.layout ||
+                     (c->mac_mode == 0 && G >= c->mac_tc_min_groups));
+    const bool tiled = !tc && (c->mac_mode == 2 || d.compact ||
+                               (c->mac_mode == 0 && G >= c->mac_min_groups));
     StageTimer tm(c, EPHDC_STAGE_MAC, st, tc || tiled ? 1 : (2 * d.Kp + 3) / 4 + 1);
     if ((c->mac_mode == 3 || d.layout) && !tc_ok) {
       e = cudaErrorNotSupported;
@@ -698,7 +705,8 @@ ephdc_status bfv_model_to_seeded(ephdc_ctx* c, const void* model, uint32_t* seed
   CHECK_CTX(c);
   CHECK_PTR(c, model, "model_dev");
   CHECK_PTR(c, seeded, "seeded_dev");
-  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0");
+  if (c->dc.layout || c->dc.compact)
+    return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0 and the full model");
   return launched(c, ephdc::launch_model_to_seeded(c->dc, (const uint32_t*)model, seeded,
                                                    (cudaStream_t)stream),
                   "model_to_seeded");
@@ -709,7 +717,8 @@ ephdc_status bfv_model_from_seeded(ephdc_ctx* c, const uint32_t* seeded, uint64_
   CHECK_CTX(c);
   CHECK_PTR(c, seeded, "seeded_dev");
   CHECK_PTR(c, model, "model_dev");
-  if (c->dc.layout) return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0");
+  if (c->dc.layout || c->dc.compact)
+    return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0 and the full model");
   return launched(c, ephdc::launch_model_from_seeded(c->dc, seeded, seed, (uint32_t*)model,
                                                      (cudaStream_t)stream),
                   "model_from_seeded");
@@ -727,7 +736,8 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* c, const void* sk, const int8_t* H
   CHECK_PTR(c, model, "model_dev");
   if (!dmax) return fail(c, EPHDC_EINVAL, "dmax is NULL");
   const DevCtx& d = c->dc;
-  if (d.layout) return fail(c, EPHDC_EUNSUPPORTED, "the noise-growth trial needs layout 0");
+  if (d.layout || d.compact)
+    return fail(c, EPHDC_EUNSUPPORTED, "the noise-growth trial needs layout 0 and the full model");
   if (d.k != 1 || d.k_in != 1 || d.r != 1)
     return fail(c, EPHDC_EUNSUPPORTED, "needs one class and the layout k_in = 1, r = 1");
   if (B < 1 || (uint32_t)B > d.cap || (uint32_t)B > c->prm.max_batch)
@@ -825,8 +835,8 @@ ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_
   if (e != cudaSuccess) return launched(c, e, "hdc_encode");
   const DevCtx& d = c->dc;
   const int G = (int)groups_for(c, B);
-  const bool tiled = c->mac_mode == 2 || (c->mac_mode == 0 && G >= c->mac_min_groups &&
-                                          G < c->mac_tc_min_groups);
+  const bool tiled = c->mac_mode == 2 || d.compact ||
+                     (c->mac_mode == 0 && G >= c->mac_min_groups && G < c->mac_tc_min_groups);
   if (c->chunk > 0 && (uint32_t)c->chunk < d.P && tiled && !d.layout && !d.scale_g) {
     // plaintext-index chunks: each chunk's plaintexts of all G groups are encoded into
     // the start of the plaintext buffer and accumulated from there, so that they could
@@ -927,9 +937,13 @@ ephdc_status ephdc_model_to_host_coeff(ephdc_ctx* c, const void* model, uint32_t
     e = cudaMalloc(&std_model, words * 4);
     if (e == cudaSuccess)
       e = ephdc::launch_unblock(d, (const uint32_t*)model, std_model, d.P, 2 * d.Kp, 0);
+  } else if (d.compact) {  // c0 only -> c0 and the regenerated c1
+    e = cudaMalloc(&std_model, words * 4);
+    if (e == cudaSuccess)
+      e = ephdc::launch_expand_compact(d, (const uint32_t*)model, std_model, 0);
   }
   if (e == cudaSuccess)
-    e = ephdc::launch_to_coeff(d, d.layout ? std_model : (const uint32_t*)model, tmp, count, 2,
+    e = ephdc::launch_to_coeff(d, std_model ? std_model : (const uint32_t*)model, tmp, count, 2,
                                (int)(2 * d.L * d.n), (int)d.n, 0, 0);
   if (e == cudaSuccess) e = cudaMemcpy(host, tmp, words * 4, cudaMemcpyDeviceToHost);
   cudaFree(tmp);
@@ -1020,6 +1034,12 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     if (v < 0 || v > 3) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1, 2 or 3");
     if (v == 3 && O > 32) return fail(c, EPHDC_EUNSUPPORTED, "tensor-core MAC needs k/k_in <= 16");
     c->mac_mode = (int)v;
+  } else if (!strcmp(knob, "model_seed")) {
+    if (v < -1) return fail(c, EPHDC_EINVAL, "model_seed must be -1 (off) or a seed >= 0");
+    if (v >= 0 && c->dc.layout)
+      return fail(c, EPHDC_EUNSUPPORTED, "the compact model needs layout 0");
+    c->dc.compact = v >= 0;
+    c->dc.model_seed = v >= 0 ? (uint64_t)v : 0;
   } else if (!strcmp(knob, "chunk")) {
     if (v < 0) return fail(c, EPHDC_EINVAL, "chunk must be >= 0");
     c->chunk = (int)v;
@@ -1027,6 +1047,8 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     if (v < 0 || v > 1) return fail(c, EPHDC_EINVAL, "layout must be 0 or 1");
     if (v == 1 && O > 32)
       return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs k/k_in <= 16");
+    if (v == 1 && c->dc.compact)
+      return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs the full model");
     c->dc.layout = (uint32_t)v;
   } else if (!strcmp(knob, "ntt_plan")) {
     if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "ntt_plan must be 0, 1 or 2");
@@ -1067,6 +1089,7 @@ int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
   if (!strcmp(knob, "ntt_plan")) return c->dc.ntt_plan;
   if (!strcmp(knob, "layout")) return c->dc.layout;
   if (!strcmp(knob, "chunk")) return c->chunk;
+  if (!strcmp(knob, "model_seed")) return c->dc.compact ? (int64_t)c->dc.model_seed : -1;
   if (!strcmp(knob, "hdc_mode")) return c->dc.hdc_mode;
   if (!strcmp(knob, "mac_splits")) return c->mac_splits;
   if (!strcmp(knob, "mac_tile"))

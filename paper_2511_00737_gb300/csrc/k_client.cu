@@ -197,7 +197,7 @@ __device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, ui
 // A chunked pass (several calls over plaintext ranges) reads plaintexts
 // [mi0, mi0 + cnt) of the model against a plaintext buffer of pP plaintexts per group
 // and adds into the accumulators (accum != 0) instead of overwriting them.
-template <int GT, int OT>
+template <int GT, int OT, bool CMP>
 __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __restrict__ pt,
                                                    const uint32_t* __restrict__ model,
                                                    uint32_t* __restrict__ acc, int G, int GC,
@@ -220,7 +220,9 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
   // piece, shared-memory word offset 4 q) belongs to thread q mod blockDim for every
   // plaintext of a chunk, so its source address is formed once per chunk and advanced
   // by a fixed stride; rows * 8 <= 4 * blockDim is checked by the launcher
-  const size_t pt_stride = L * n, model_stride = (size_t)O * L * n;
+  // the compact model stores c0 only ([P][O/2][L][n]); its c1 rows are generated
+  const size_t pt_stride = L * n;
+  const size_t model_stride = (size_t)(CMP ? O / 2 : O) * L * n;
   auto load_chunk = [&](int b, uint32_t i0) {
     uint32_t* dst = sm + b * buf_words;
 #pragma unroll
@@ -229,16 +231,41 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
       if (q < rows * 8) {
         const int rr = q >> 3, piece = q & 7;
         const bool is_pt = rr < GC;
+        const int o = rr - GC;
+        if (!is_pt && CMP && (o & 1)) continue;  // c1: generated below
         const bool gok = !is_pt || g0 + rr < G;
         const size_t stride = is_pt ? pt_stride : model_stride;
+        const int mrow = CMP ? o >> 1 : o;
         const uint32_t* src =
             is_pt ? pt + ((size_t)(gok ? g0 + rr : 0) * P * L + l) * n + k0 + piece * 4
-                  : model + ((size_t)(rr - GC) * L + l) * n + k0 + piece * 4 +
+                  : model + ((size_t)mrow * L + l) * n + k0 + piece * 4 +
                         (size_t)mi0 * model_stride;
         src += (size_t)i0 * stride;
         for (int ii = 0; ii < IC; ii++, src += stride) {
           const bool ok = gok && i0 + ii < CNT;
           cp_async16_zfill(dst + ii * rows * 32 + 4 * q, ok ? src : pt, ok);
+        }
+      }
+    }
+    if (CMP) {
+      // c1 of model ciphertext (i, j') at device position k of limb l: 64-bit word
+      // l n + k of the stream (model seed, domain 8, i Kp + j') mod q_l; one ChaCha20
+      // block gives the 8 coefficients of an item (plaintext, j', 8 of the 32 columns)
+      const int kp = O / 2, items = IC * kp * 4;
+      for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int ii = it / (kp * 4), rem = it - ii * kp * 4, jp = rem >> 2, cb = rem & 3;
+        uint32_t* d = dst + ii * rows * 32 + (GC + 2 * jp + 1) * 32 + 8 * cb;
+        const uint32_t li = i0 + ii;
+        if (li < CNT) {
+          uint32_t w[16];
+          chacha_block(c.model_seed, 8, (uint64_t)(mi0 + li) * kp + jp,
+                       (uint32_t)(((size_t)l * n + k0 + 8 * cb) / 8), w);
+#pragma unroll
+          for (int u = 0; u < 8; u++)
+            d[u] = red64((uint64_t)w[2 * u] | ((uint64_t)w[2 * u + 1] << 32), p, mu);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; u++) d[u] = 0;
         }
       }
     }
@@ -499,12 +526,12 @@ static cudaError_t run_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, con
   const size_t smem = 2 * (size_t)IC * (GC + O) * 32 * sizeof(uint32_t);
   if (warps < 1 || warps > 16 || GC % GT || (GC + O) * 8 > 4 * warps * 32)
     return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_mac_tiled<GT, OT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = c.compact ? k_mac_tiled<GT, OT, true> : k_mac_tiled<GT, OT, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(c.n / 32, c.L, (G + GC - 1) / GC);
-  k_mac_tiled<GT, OT><<<grid, warps * 32, smem, st>>>(c, pt, model, acc, G, GC, IC, pP, mi0,
-                                                       cnt, accum);
+  kern<<<grid, warps * 32, smem, st>>>(c, pt, model, acc, G, GC, IC, pP, mi0, cnt, accum);
   return cudaGetLastError();
 }
 

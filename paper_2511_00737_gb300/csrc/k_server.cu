@@ -103,7 +103,11 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
     }
     mb[padi(x)] = v;
   }
-  fill_uniform(c, seed, 2, cidx, l, ab);
+  // c1: the standard model draws a in the coefficient domain (domain 2) and transforms
+  // it; the compact model draws it in the evaluation domain at device position k
+  // (domain 8, word l n + k), so that the multiply-accumulate can regenerate it
+  if (c.compact) fill_uniform(c, c.model_seed, 8, cidx, l, ab);
+  else fill_uniform(c, seed, 2, cidx, l, ab);
   fill_gauss(c, seed, 3, cidx, m.p, eb);
   __syncthreads();
   ntt_inv_smem(mb, c.logn, c.mt);  // m in [0, t)
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
   for (uint32_t x = threadIdx.x; x < c.n; x += blockDim.x) mb[padi(x)] = scaled(mb[padi(x)]);
   __syncthreads();
   ntt_fwd_smem(mb, c.logn, m);
-  ntt_fwd_smem(ab, c.logn, m);
+  if (!c.compact) ntt_fwd_smem(ab, c.logn, m);
   ntt_fwd_smem(eb, c.logn, m);
   const uint32_t* s = sk + (size_t)l * c.n;
   uint32_t* c0 = model + ((size_t)(cidx * 2 + 0) * c.L + l) * c.n;
@@ -123,7 +127,9 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
     const uint32_t a = ab[padi(x)];
     uint32_t v = subm(eb[padi(x)], mulm(a, s[x], m), m.p);
     v = addm(v, mb[padi(x)], m.p);
-    if (c.layout) {  // outputs o = j' * 2 + poly of plaintext i
+    if (c.compact) {  // c0 only, [P][O/2][L][n]
+      model[((size_t)cidx * c.L + l) * c.n + x] = v;
+    } else if (c.layout) {  // outputs o = j' * 2 + poly of plaintext i
       model[blk_index(c.n, c.P, O, i, jp * 2, l, x)] = v;
       model[blk_index(c.n, c.P, O, i, jp * 2 + 1, l, x)] = a;
     } else {
@@ -325,6 +331,30 @@ __global__ void __launch_bounds__(512) k_ntt_natural(DevCtx c, uint32_t limb, ui
   }
 }
 
+// compact model [P][O/2][L][n] (c0 only) -> the whole model [P][O/2][2][L][n] with c1
+// regenerated from the model seed (host-format conversions)
+__global__ void k_expand_compact(DevCtx c, const uint32_t* __restrict__ c0,
+                                 uint32_t* __restrict__ full, size_t blocks) {
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < blocks;
+       x += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t b = (uint32_t)(x % (c.n / 8));
+    size_t rest = x / (c.n / 8);
+    const uint32_t l = (uint32_t)(rest % c.L);
+    const size_t cidx = rest / c.L;
+    uint32_t w[16];
+    chacha_block(c.model_seed, 8, cidx, (uint32_t)(((size_t)l * c.n) / 8 + b), w);
+    const uint32_t* src = c0 + (cidx * c.L + l) * c.n + 8 * b;
+    uint32_t* d0 = full + ((cidx * 2) * c.L + l) * c.n + 8 * b;
+    uint32_t* d1 = full + ((cidx * 2 + 1) * c.L + l) * c.n + 8 * b;
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      d0[u] = src[u];
+      d1[u] = red64((uint64_t)w[2 * u] | ((uint64_t)w[2 * u + 1] << 32), c.mq[l].p,
+                    c.mq[l].mu);
+    }
+  }
+}
+
 // blocked [L][n/4][A][B][4] -> standard [A][B][L][n] (host-format conversions)
 __global__ void k_unblock(DevCtx c, const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
                           uint32_t A, uint32_t B, size_t words) {
@@ -399,6 +429,14 @@ cudaError_t launch_decrypt_phases(const DevCtx& c, uint32_t* xbuf, int count, in
   if (e != cudaSuccess) return e;
   k_dec_round<<<dim3(count, (c.n + 255) / 256), 256, 0, st>>>(c, xbuf);
   k_dec_scores<<<count, ntt_threads(c), s1, st>>>(c, xbuf, B, scores);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_compact(const DevCtx& c, const uint32_t* c0, uint32_t* full,
+                                  cudaStream_t st) {
+  const size_t blocks = (size_t)c.P * c.Kp * c.L * (c.n / 8);
+  const unsigned grid = (unsigned)((blocks + 255) / 256 < 152 * 32 ? (blocks + 255) / 256 : 152 * 32);
+  k_expand_compact<<<grid, 256, 0, st>>>(c, c0, full, blocks);
   return cudaGetLastError();
 }
 
