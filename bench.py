@@ -68,6 +68,10 @@ def parse():
                          "at a time (0 = the whole pass at once)")
     ap.add_argument("--compact", action="store_true",
                     help="the compact model: c0 stored, c1 regenerated by the tiled MAC")
+    ap.add_argument("--model-digits", type=int, default=-1,
+                    help="1: the digit model (fp16 operand of the model's signed digits, read "
+                         "by the digit-outer-product tensor-core MAC), 0: residues; default: "
+                         "digits for dense65536, dense65536_r8 and clients64")
     ap.add_argument("--no-legs", action="store_true",
                     help="time only the headline workload (not clients64, serve, dense65536)")
     return ap.parse_args()
@@ -214,6 +218,7 @@ def config_of(w, B, per_step=None):
 
 # ------------------------------------------------------------------ parity of the timed work
 DIGESTS = {"face1024": "face1024x16", "clients64": "clients64", "dense65536": "dense65536"}
+DIGIT_WORKLOADS = ("dense65536", "dense65536_r8", "clients64")
 
 
 def digest_check(out, ctx, name):
@@ -272,6 +277,12 @@ def run_ours(args, w, B):
     # the compact model: only c0 stored, c1 regenerated by the multiply-accumulate
     model_seed = seed if args.compact else -1
     ctx.tune_set("model_seed", model_seed)
+    # the digit model (the model's signed base-256 digits as the tensor-core operand):
+    # by default where many groups share each model read and k/k_in fills the MMA rows
+    # (dense65536: MAC 15.5 ms vs 30.4 ms; clients64: 3.4 ms vs 4.2 ms), residues for the
+    # 4-output face1024 step
+    mdig = args.model_digits if args.model_digits >= 0 else int(w.name in DIGIT_WORKLOADS)
+    ctx.tune_set("model_digits", mdig)
     if args.mac_mode >= 0:
         ctx.tune_set("mac_mode", args.mac_mode)
     if args.hdc_mode >= 0:
@@ -305,6 +316,7 @@ def run_ours(args, w, B):
         for cx in ctxs[1:]:
             cx.tune_set("layout", layout)
             cx.tune_set("model_seed", model_seed)
+            cx.tune_set("model_digits", mdig)
             AT.apply(cx, tuned)
         pipes = [pipe] + [BT.GraphedPipeline(cx, Wt, model, gk, max_groups=ctx.groups(B))
                           for cx in ctxs[1:]]
@@ -340,6 +352,7 @@ def run_ours(args, w, B):
         for cx in ctxs[1:]:
             cx.tune_set("layout", layout)  # the shared model's layout and form
             cx.tune_set("model_seed", model_seed)
+            cx.tune_set("model_digits", mdig)
             if tuned:
                 AT.apply(cx, tuned)
         for cx in ctxs:
@@ -531,6 +544,9 @@ def run_ours(args, w, B):
         if args.compact:
             line["config"]["model"] = ("compact: c0 stored, c1 regenerated from the seed by "
                                        "the multiply-accumulate")
+        if mdig:
+            line["config"]["model"] = ("digit model: fp16 tensor-core operand of the signed "
+                                       "base-256 digits")
         if not multi and tuned:
             line["config"]["mac_schedule"] = tuned
         if multi:

@@ -222,6 +222,15 @@ ephdc_status bfv_model_to_seeded(ephdc_ctx* ctx, const void* model_dev, uint32_t
 ephdc_status bfv_model_from_seeded(ephdc_ctx* ctx, const uint32_t* seeded_dev, uint64_t seed,
                                    void* model_dev, void* stream);
 
+/* Client: the digit model (see the knob "model_digits") from a model in the standard
+ * device order, model_dev as bfv_encrypt_model produces it with "model_digits" 0 and
+ * "layout" 0 ([P][k/k_in][2][L][n] NTT-domain residues, ephdc_model_bytes of such a
+ * context); model_digits_dev holds ephdc_model_bytes of this context, which must have
+ * "model_digits" 1 (else EPHDC_EUNSUPPORTED).  Equal to what bfv_encrypt_model writes
+ * for the same ciphertexts under "model_digits" 1. */
+ephdc_status bfv_model_to_digits(ephdc_ctx* ctx, const void* model_dev, void* model_digits_dev,
+                                 void* stream);
+
 /* ---------------------------------------------------------------- server-side variant */
 /* HE-HDC-SR (Sec. 3, the comparison of Sec. 6, Table t:clientrt): the roles of the
  * client-side path swapped.  The CLIENT holds the secret key and encrypts its query
@@ -273,7 +282,9 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
 
 /* Schedule knobs of the multi-accumulate (set by the autotuner; results never
  * change): "mac_mode" 0 automatic / 1 streaming / 2 tiled / 3 tensor cores (exact
- * signed-digit split, k/k_in <= 16), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
+ * signed-digit split, k/k_in <= 16) / 4 tensor cores on the digit model (see
+ * "model_digits"), "mac_cluster" 0, 1, 2, 4 or 8 (the digit-model product: CTAs of
+ * consecutive group blocks that share each model block by multicast, 0 = 4), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
  * cores from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
  * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
  * warp, groups per CTA, plaintexts per staged chunk, at most 15); "hdc_mode" 0..3 is
@@ -303,6 +314,20 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * with the seed the model is encrypted with, on every context that uses the model and
  * before bfv_encrypt_model; the blocked layout, the seeded model message, the noise-growth
  * trial and bfv_ptct_similarity_noalloc do not take it (EPHDC_EUNSUPPORTED).
+ * "model_digits" 1 selects the digit model (needs k/k_in <= 16, layout 0 and the full
+ * model): the model is stored as the fp16 tensor-core operand of the signed base-256
+ * digits d_v of every residue (x = sum_{v<4} d_v 2^(8v), d_v = byte v of x + 0x80808080
+ * less 128, |d_v| <= 128), so that the multiply-accumulate copies it into shared memory
+ * without splitting it; ephdc_model_bytes = L n ceil(P/16) 4096 (twice the residue
+ * model at k/k_in = 16).  Order: fp16 tiles of 128 rows x 16 columns, tile
+ * ((l (n/8) + x/8) ceil(P/16) + i/16) 8 + x%8 for coefficient x of limb l and plaintext
+ * i; row 32 v + o, column i%16 at byte (row/8) 256 + (column/8) 128 + (row%8) 16 +
+ * (column%8) 2; rows of outputs o >= 2 k/k_in and columns of plaintexts i >= P are zero.
+ * Set it before bfv_encrypt_model (or convert a residue model with
+ * bfv_model_to_digits); the multiply-accumulate then runs "mac_mode" 4 (0 or 4 accepted,
+ * others EPHDC_EUNSUPPORTED), and the seeded model message, the compact model, the
+ * blocked layout, the noise-growth trial and bfv_ptct_similarity_noalloc return
+ * EPHDC_EUNSUPPORTED.  ephdc_model_to_host_coeff reassembles the residues.
  * EPHDC_EINVAL for an unknown knob or an invalid value.  ephdc_tune_get returns -1 for
  * an unknown knob. */
 ephdc_status ephdc_tune_set(ephdc_ctx* ctx, const char* knob, int64_t value);

@@ -8,6 +8,8 @@ over plaintext ranges (several split caps), and the tiled multi-group kernel wit
 2 or 4 groups and 4, 7 or 8 outputs per warp, 8 to 64 groups per CTA and 4 to 15
 plaintexts per staged chunk, and the exact signed-digit product on the tensor cores
 (the only candidate when the context stores plaintexts and model coefficient-blocked).
+A context with the digit model has one product, the digit outer product on the tensor
+cores; its candidates are the cluster sizes that share each model block.
 """
 import json
 import os
@@ -20,9 +22,9 @@ CACHE = os.environ.get("EPHDC_TUNE_CACHE",
 
 def _key(ctx, G):
     name = torch.cuda.get_device_name(ctx.device).replace(" ", "_")
-    return "%s|n%d|L%d|k%d|kin%d|r%d|G%d|lay%d|cm%d" % (
+    return "%s|n%d|L%d|k%d|kin%d|r%d|G%d|lay%d|cm%d|md%d" % (
         name, ctx.n, ctx.L, ctx.k, ctx.k_in, ctx.r, G, ctx.tune_get("layout"),
-        int(ctx.tune_get("model_seed") >= 0))
+        int(ctx.tune_get("model_seed") >= 0), ctx.tune_get("model_digits"))
 
 
 def _load():
@@ -44,6 +46,9 @@ def candidates(ctx, G):
     O = 2 * ctx.Kp
     if ctx.tune_get("layout") == 1:
         return [{"mac_mode": 3}]   # the blocked layout is read by the tensor cores only
+    if ctx.tune_get("model_digits") == 1:   # read by the digit outer product only
+        blocks = -(-G // 16)
+        return [{"mac_mode": 4, "mac_cluster": c} for c in (1, 2, 4) if c == 1 or c < 2 * blocks]
     compact = ctx.tune_get("model_seed") >= 0  # regenerated by the tiled kernel only
     if compact and G < 2:
         return [{"mac_mode": 2}]

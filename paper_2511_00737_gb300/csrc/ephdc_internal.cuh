@@ -76,7 +76,29 @@ struct DevCtx {
   // multiply-accumulate as it reads the model
   uint32_t compact;
   uint64_t model_seed;
+  // digit model: the model is stored as the tensor-core operand of its signed base-256
+  // digits, fp16 tiles [L][n/8][P16][8][128 x 16] (P16 = ceil(P/16); tile (l, x/8, i/16,
+  // x%8) holds rows r = 32 v + o, columns i%16, at mdig_off(r, i%16); rows o >= O and
+  // plaintexts i >= P are zero), read by the digit-outer-product multiply-accumulate
+  uint32_t mdig;
 };
+
+// byte offset of element (row r, column k) of a 16-column fp16 operand tile in the
+// K-major layout without swizzle that tcgen05 descriptors with LBO = 128 and SBO = 256
+// describe: 8 x 8 core matrices of 128 bytes, the two column halves 128 bytes apart,
+// consecutive 8-row groups 256 bytes apart
+__host__ __device__ __forceinline__ uint32_t mdig_off(uint32_t r, uint32_t k) {
+  return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// fp16 word index of digit v of model residue (plaintext i, output o, limb l,
+// coefficient x) in the digit model
+__host__ __device__ __forceinline__ size_t mdig_index(uint32_t n, uint32_t P, uint32_t i,
+                                                      uint32_t o, uint32_t v, uint32_t l,
+                                                      uint32_t x) {
+  const uint32_t P16 = (P + 15) / 16;
+  const size_t tile = (((size_t)l * (n >> 3) + (x >> 3)) * P16 + (i >> 4)) * 8 + (x & 7);
+  return tile * 2048 + mdig_off(32 * v + o, i & 15) / 2;
+}
 
 // word index of coefficient k of limb l of pair (a, b) in the blocked layout
 // [L][n/4][A][B][4] (plaintexts: a = group, b = plaintext; model: a = plaintext,
@@ -724,6 +746,8 @@ cudaError_t launch_mac_tiled(const DevCtx& c, const uint32_t* pt, int G, const u
 // the same accumulators through the exact byte-split tensor-core product (k/k_in <= 16)
 cudaError_t launch_mac_tc(const DevCtx& c, const uint32_t* pt, int G, const uint32_t* model,
                           uint32_t* acc, cudaStream_t st);
+cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint16_t* model,
+                          uint32_t* acc, int cluster, cudaStream_t st);
 cudaError_t launch_rotate_sum(const DevCtx& c, uint32_t* acc, uint32_t* tmp, uint32_t* digits,
                               int count, const uint32_t* gk, cudaStream_t st);
 cudaError_t launch_export(const DevCtx& c, const uint32_t* acc, int count, uint32_t* out,
@@ -763,6 +787,10 @@ cudaError_t launch_unblock(const DevCtx& c, const uint32_t* src, uint32_t* dst, 
                            uint32_t B, cudaStream_t st);
 cudaError_t launch_expand_compact(const DevCtx& c, const uint32_t* c0, uint32_t* full,
                                   cudaStream_t st);
+cudaError_t launch_undigit(const DevCtx& c, const uint16_t* mdig, uint32_t* model,
+                           cudaStream_t st);
+cudaError_t launch_model_to_digits(const DevCtx& c, const uint32_t* model, uint16_t* mdig,
+                                   cudaStream_t st);
 cudaError_t launch_to_coeff(const DevCtx& c, const uint32_t* in, uint32_t* out, int count,
                             int limbs_per_item, int in_stride_words, int limb_stride_words,
                             int limb0_is_digit_major, cudaStream_t st);

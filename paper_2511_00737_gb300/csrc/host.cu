@@ -126,6 +126,8 @@ struct ephdc_ctx {
   int mac_tc_min_groups = 1 << 30;
   int mac_splits = 0;      // streaming: split count cap (0 = heuristic)
   ephdc::MacTiling tile = {4, 8, 32, 8};
+  // digit-outer-product MAC: CTAs per cluster sharing each model block (0 = 4)
+  int mac_cluster = 0;
   // ephdc_infer with the tiled MAC: encode and accumulate this many plaintext indices
   // of every group at a time into a reused buffer (0 = the whole pass at once)
   int chunk = 0;
@@ -515,9 +517,11 @@ size_t ephdc_galois_key_bytes(const ephdc_ctx* c) {
   return c ? (size_t)c->dc.logr * c->dc.L * c->dc.L * 4 * c->dc.n * sizeof(uint32_t) : 0;
 }
 size_t ephdc_model_bytes(const ephdc_ctx* c) {
-  return c ? (size_t)c->dc.P * c->dc.Kp * (c->dc.compact ? 1 : 2) * c->dc.L * c->dc.n *
-                 sizeof(uint32_t)
-           : 0;
+  if (!c) return 0;
+  // the digit model: 4 KB per (limb, coefficient, 16 plaintexts)
+  if (c->dc.mdig) return (size_t)c->dc.L * c->dc.n * ((c->dc.P + 15) / 16) * 4096;
+  return (size_t)c->dc.P * c->dc.Kp * (c->dc.compact ? 1 : 2) * c->dc.L * c->dc.n *
+         sizeof(uint32_t);
 }
 size_t ephdc_plain_bytes(const ephdc_ctx* c, int32_t B) {
   if (!c || B < 1) return 0;
@@ -582,6 +586,20 @@ static ephdc_status similarity_impl(ephdc_ctx* c, const uint32_t* pt, int32_t B,
       return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs mac_mode 0 or 3");
     if (d.compact && (c->mac_mode == 1 || c->mac_mode == 3))
       return fail(c, EPHDC_EUNSUPPORTED, "the compact model needs mac_mode 0 or 2");
+    // the digit model is read by the digit-outer-product product only, which reads
+    // nothing else
+    if (d.mdig != (c->mac_mode == 4) && !(d.mdig && c->mac_mode == 0))
+      return fail(c, EPHDC_EUNSUPPORTED,
+                  d.mdig ? "the digit model needs mac_mode 0 or 4"
+                         : "mac_mode 4 needs the digit model (knob model_digits)");
+    if (d.mdig) {
+      {
+        StageTimer tm(c, EPHDC_STAGE_MAC, st, 1);
+        e = ephdc::launch_mac_uv(d, pt, G, (const uint16_t*)model, c->acc, c->mac_cluster, st);
+      }
+      if (e != cudaSuccess) return launched(c, e, "ptct_mac");
+      return rotate_export(c, G, gk, out, st);
+    }
     const bool tc = !d.compact && tc_ok &&
                     (c->mac_mode == 3 || d.layout ||
                      (c->mac_mode == 0 && G >= c->mac_tc_min_groups));
@@ -699,13 +717,25 @@ ephdc_status bfv_ptct_similarity(ephdc_ctx* c, const uint32_t* pt, int32_t B, co
   return similarity_impl(c, pt, B, model, gk, out, (cudaStream_t)stream);
 }
 
+ephdc_status bfv_model_to_digits(ephdc_ctx* c, const void* model, void* model_digits,
+                                 void* stream) {
+  CHECK_CTX(c);
+  CHECK_PTR(c, model, "model_dev");
+  CHECK_PTR(c, model_digits, "model_digits_dev");
+  if (!c->dc.mdig)
+    return fail(c, EPHDC_EUNSUPPORTED, "the destination is a digit model: set model_digits 1");
+  return launched(c, ephdc::launch_model_to_digits(c->dc, (const uint32_t*)model,
+                                                   (uint16_t*)model_digits, (cudaStream_t)stream),
+                  "model_to_digits");
+}
+
 // ------------------------------------------------------------------ seeded model message
 ephdc_status bfv_model_to_seeded(ephdc_ctx* c, const void* model, uint32_t* seeded,
                                  void* stream) {
   CHECK_CTX(c);
   CHECK_PTR(c, model, "model_dev");
   CHECK_PTR(c, seeded, "seeded_dev");
-  if (c->dc.layout || c->dc.compact)
+  if (c->dc.layout || c->dc.compact || c->dc.mdig)
     return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0 and the full model");
   return launched(c, ephdc::launch_model_to_seeded(c->dc, (const uint32_t*)model, seeded,
                                                    (cudaStream_t)stream),
@@ -717,7 +747,7 @@ ephdc_status bfv_model_from_seeded(ephdc_ctx* c, const uint32_t* seeded, uint64_
   CHECK_CTX(c);
   CHECK_PTR(c, seeded, "seeded_dev");
   CHECK_PTR(c, model, "model_dev");
-  if (c->dc.layout || c->dc.compact)
+  if (c->dc.layout || c->dc.compact || c->dc.mdig)
     return fail(c, EPHDC_EUNSUPPORTED, "the seeded message needs layout 0 and the full model");
   return launched(c, ephdc::launch_model_from_seeded(c->dc, seeded, seed, (uint32_t*)model,
                                                      (cudaStream_t)stream),
@@ -736,7 +766,7 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* c, const void* sk, const int8_t* H
   CHECK_PTR(c, model, "model_dev");
   if (!dmax) return fail(c, EPHDC_EINVAL, "dmax is NULL");
   const DevCtx& d = c->dc;
-  if (d.layout || d.compact)
+  if (d.layout || d.compact || d.mdig)
     return fail(c, EPHDC_EUNSUPPORTED, "the noise-growth trial needs layout 0 and the full model");
   if (d.k != 1 || d.k_in != 1 || d.r != 1)
     return fail(c, EPHDC_EUNSUPPORTED, "needs one class and the layout k_in = 1, r = 1");
@@ -835,8 +865,9 @@ ephdc_status ephdc_infer(ephdc_ctx* c, const int8_t* X, const int8_t* Wt, int32_
   if (e != cudaSuccess) return launched(c, e, "hdc_encode");
   const DevCtx& d = c->dc;
   const int G = (int)groups_for(c, B);
-  const bool tiled = c->mac_mode == 2 || d.compact ||
-                     (c->mac_mode == 0 && G >= c->mac_min_groups && G < c->mac_tc_min_groups);
+  const bool tiled =
+      !d.mdig && (c->mac_mode == 2 || d.compact ||
+                  (c->mac_mode == 0 && G >= c->mac_min_groups && G < c->mac_tc_min_groups));
   if (c->chunk > 0 && (uint32_t)c->chunk < d.P && tiled && !d.layout && !d.scale_g) {
     // plaintext-index chunks: each chunk's plaintexts of all G groups are encoded into
     // the start of the plaintext buffer and accumulated from there, so that they could
@@ -941,6 +972,9 @@ ephdc_status ephdc_model_to_host_coeff(ephdc_ctx* c, const void* model, uint32_t
     e = cudaMalloc(&std_model, words * 4);
     if (e == cudaSuccess)
       e = ephdc::launch_expand_compact(d, (const uint32_t*)model, std_model, 0);
+  } else if (d.mdig) {  // digits -> residues
+    e = cudaMalloc(&std_model, words * 4);
+    if (e == cudaSuccess) e = ephdc::launch_undigit(d, (const uint16_t*)model, std_model, 0);
   }
   if (e == cudaSuccess)
     e = ephdc::launch_to_coeff(d, std_model ? std_model : (const uint32_t*)model, tmp, count, 2,
@@ -1031,13 +1065,24 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
   if (!knob) return fail(c, EPHDC_EINVAL, "knob is NULL");
   const int O = 2 * (int)c->dc.Kp;
   if (!strcmp(knob, "mac_mode")) {
-    if (v < 0 || v > 3) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1, 2 or 3");
-    if (v == 3 && O > 32) return fail(c, EPHDC_EUNSUPPORTED, "tensor-core MAC needs k/k_in <= 16");
+    if (v < 0 || v > 4) return fail(c, EPHDC_EINVAL, "mac_mode must be 0, 1, 2, 3 or 4");
+    if (v >= 3 && O > 32) return fail(c, EPHDC_EUNSUPPORTED, "tensor-core MAC needs k/k_in <= 16");
     c->mac_mode = (int)v;
+  } else if (!strcmp(knob, "model_digits")) {
+    if (v < 0 || v > 1) return fail(c, EPHDC_EINVAL, "model_digits must be 0 or 1");
+    if (v == 1 && O > 32)
+      return fail(c, EPHDC_EUNSUPPORTED, "the digit model needs k/k_in <= 16");
+    if (v == 1 && (c->dc.layout || c->dc.compact))
+      return fail(c, EPHDC_EUNSUPPORTED, "the digit model needs layout 0 and the full model");
+    c->dc.mdig = (uint32_t)v;
+  } else if (!strcmp(knob, "mac_cluster")) {
+    if (v != 0 && v != 1 && v != 2 && v != 4 && v != 8)
+      return fail(c, EPHDC_EINVAL, "mac_cluster must be 0, 1, 2, 4 or 8");
+    c->mac_cluster = (int)v;
   } else if (!strcmp(knob, "model_seed")) {
     if (v < -1) return fail(c, EPHDC_EINVAL, "model_seed must be -1 (off) or a seed >= 0");
-    if (v >= 0 && c->dc.layout)
-      return fail(c, EPHDC_EUNSUPPORTED, "the compact model needs layout 0");
+    if (v >= 0 && (c->dc.layout || c->dc.mdig))
+      return fail(c, EPHDC_EUNSUPPORTED, "the compact model needs layout 0 and residues");
     c->dc.compact = v >= 0;
     c->dc.model_seed = v >= 0 ? (uint64_t)v : 0;
   } else if (!strcmp(knob, "chunk")) {
@@ -1047,8 +1092,8 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     if (v < 0 || v > 1) return fail(c, EPHDC_EINVAL, "layout must be 0 or 1");
     if (v == 1 && O > 32)
       return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs k/k_in <= 16");
-    if (v == 1 && c->dc.compact)
-      return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs the full model");
+    if (v == 1 && (c->dc.compact || c->dc.mdig))
+      return fail(c, EPHDC_EUNSUPPORTED, "the blocked layout needs the full residue model");
     c->dc.layout = (uint32_t)v;
   } else if (!strcmp(knob, "ntt_plan")) {
     if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "ntt_plan must be 0, 1 or 2");
@@ -1088,6 +1133,8 @@ int64_t ephdc_tune_get(const ephdc_ctx* c, const char* knob) {
   if (!strcmp(knob, "mac_tc_min_groups")) return c->mac_tc_min_groups;
   if (!strcmp(knob, "ntt_plan")) return c->dc.ntt_plan;
   if (!strcmp(knob, "layout")) return c->dc.layout;
+  if (!strcmp(knob, "model_digits")) return c->dc.mdig;
+  if (!strcmp(knob, "mac_cluster")) return c->mac_cluster;
   if (!strcmp(knob, "chunk")) return c->chunk;
   if (!strcmp(knob, "model_seed")) return c->dc.compact ? (int64_t)c->dc.model_seed : -1;
   if (!strcmp(knob, "hdc_mode")) return c->dc.hdc_mode;

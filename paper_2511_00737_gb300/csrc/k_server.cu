@@ -7,6 +7,8 @@
 //   domain 4/5: uniform a / Gaussian e of Galois key (fold step j, digit i), obj j<<16|i
 // A uniform coefficient (limb l, index k) is 64-bit word l*n + k mod q_l; a Gaussian
 // coefficient k inverts the cumulative table at 64-bit word k.
+#include <cuda_fp16.h>
+
 #include "ephdc_internal.cuh"
 
 namespace {
@@ -74,6 +76,17 @@ __global__ void __launch_bounds__(512) k_galois_keys(DevCtx c, uint64_t seed,
   }
 }
 
+// digit v of residue `val` (balanced base 256: byte v of val + 0x80808080, less 128) as
+// the fp16 element of the digit model, for v < 4
+__device__ __forceinline__ void store_digits(const DevCtx& c, uint16_t* mdig, uint32_t i,
+                                             uint32_t o, uint32_t l, uint32_t x, uint32_t val) {
+  const uint32_t vb = val + 0x80808080u;
+#pragma unroll
+  for (uint32_t v = 0; v < 4; v++)
+    mdig[mdig_index(c.n, c.P, i, o, v, l, x)] =
+        __half_as_ushort(__int2half_rn((int)((vb >> (8 * v)) & 255u) - 128));
+}
+
 // ------------------------------------------------------------------ model encryption
 // One CTA per (ciphertext i*Kp + jp, limb l).  Class value c_{jp*k_in+jin}[i*r+ch] fills
 // slot (rho, ch*W + jin*cap_row + qq) for all qq < cap_row; encode with the inverse NTT
@@ -129,6 +142,9 @@ __global__ void __launch_bounds__(512) k_encrypt_model(DevCtx c, const int8_t* _
     v = addm(v, mb[padi(x)], m.p);
     if (c.compact) {  // c0 only, [P][O/2][L][n]
       model[((size_t)cidx * c.L + l) * c.n + x] = v;
+    } else if (c.mdig) {  // the signed base-256 digits of c0 and c1 as fp16 operand rows
+      store_digits(c, reinterpret_cast<uint16_t*>(model), i, jp * 2, l, x, v);
+      store_digits(c, reinterpret_cast<uint16_t*>(model), i, jp * 2 + 1, l, x, a);
     } else if (c.layout) {  // outputs o = j' * 2 + poly of plaintext i
       model[blk_index(c.n, c.P, O, i, jp * 2, l, x)] = v;
       model[blk_index(c.n, c.P, O, i, jp * 2 + 1, l, x)] = a;
@@ -355,6 +371,41 @@ __global__ void k_expand_compact(DevCtx c, const uint32_t* __restrict__ c0,
   }
 }
 
+// standard [P][O][L][n] -> digit model (the padding is zeroed by the launcher)
+__global__ void k_todigits(DevCtx c, const uint32_t* __restrict__ src, uint16_t* __restrict__ mdig,
+                           size_t words) {
+  const uint32_t O = 2 * c.Kp;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < words;
+       x += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = (uint32_t)(x % c.n);
+    size_t rest = x / c.n;
+    const uint32_t l = (uint32_t)(rest % c.L);
+    rest /= c.L;
+    const uint32_t o = (uint32_t)(rest % O), i = (uint32_t)(rest / O);
+    store_digits(c, mdig, i, o, l, k, src[x]);
+  }
+}
+
+// digit model -> standard [P][O][L][n]: residue = sum_v d_v 2^(8v) (exact: the digits
+// of a residue in [0, q_l) reassemble it)
+__global__ void k_undigit(DevCtx c, const uint16_t* __restrict__ mdig, uint32_t* __restrict__ dst,
+                          size_t words) {
+  const uint32_t O = 2 * c.Kp;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < words;
+       x += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t k = (uint32_t)(x % c.n);
+    size_t rest = x / c.n;
+    const uint32_t l = (uint32_t)(rest % c.L);
+    rest /= c.L;
+    const uint32_t o = (uint32_t)(rest % O), i = (uint32_t)(rest / O);
+    int64_t r = 0;
+    for (uint32_t v = 0; v < 4; v++)
+      r += (int64_t)__half2int_rn(__ushort_as_half(mdig[mdig_index(c.n, c.P, i, o, v, l, k)]))
+           << (8 * v);
+    dst[x] = (uint32_t)r;
+  }
+}
+
 // blocked [L][n/4][A][B][4] -> standard [A][B][L][n] (host-format conversions)
 __global__ void k_unblock(DevCtx c, const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
                           uint32_t A, uint32_t B, size_t words) {
@@ -389,6 +440,10 @@ cudaError_t launch_encrypt_model(const DevCtx& c, const int8_t* classes, const u
   const size_t s = 3 * padded_words(c.n) * 4;
   cudaError_t e = set_smem(k_encrypt_model, s);
   if (e != cudaSuccess) return e;
+  if (c.mdig) {  // the digit model's padding rows and plaintexts are zero
+    e = cudaMemsetAsync(model, 0, (size_t)c.L * c.n * ((c.P + 15) / 16) * 4096, st);
+    if (e != cudaSuccess) return e;
+  }
   k_encrypt_model<<<dim3(c.P * c.Kp, c.L), ntt_threads(c), s, st>>>(c, classes, sk, seed, model);
   return cudaGetLastError();
 }
@@ -437,6 +492,23 @@ cudaError_t launch_expand_compact(const DevCtx& c, const uint32_t* c0, uint32_t*
   const size_t blocks = (size_t)c.P * c.Kp * c.L * (c.n / 8);
   const unsigned grid = (unsigned)((blocks + 255) / 256 < 152 * 32 ? (blocks + 255) / 256 : 152 * 32);
   k_expand_compact<<<grid, 256, 0, st>>>(c, c0, full, blocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_model_to_digits(const DevCtx& c, const uint32_t* model, uint16_t* mdig,
+                                   cudaStream_t st) {
+  const size_t words = (size_t)c.P * 2 * c.Kp * c.L * c.n;
+  cudaError_t e =
+      cudaMemsetAsync(mdig, 0, (size_t)c.L * c.n * ((c.P + 15) / 16) * 4096, st);
+  if (e != cudaSuccess) return e;
+  k_todigits<<<1024, 256, 0, st>>>(c, model, mdig, words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_undigit(const DevCtx& c, const uint16_t* mdig, uint32_t* model,
+                           cudaStream_t st) {
+  const size_t words = (size_t)c.P * 2 * c.Kp * c.L * c.n;
+  k_undigit<<<1024, 256, 0, st>>>(c, mdig, model, words);
   return cudaGetLastError();
 }
 

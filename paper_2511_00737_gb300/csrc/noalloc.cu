@@ -47,9 +47,9 @@ extern "C" ephdc_status bfv_ptct_similarity_noalloc(ephdc_ctx* ctx, const uint32
   if (!aligned16(pt) || !aligned16(model) || !aligned16(out) || (gk && !aligned16(gk)))
     return ephdc::ctx_fail(ctx, EPHDC_EINVAL, "device pointers must be 16-byte aligned");
   if (B < 1) return ephdc::ctx_fail(ctx, EPHDC_EINVAL, "batch must be positive");
-  if (d.layout || d.compact)
+  if (d.layout || d.compact || d.mdig)
     return ephdc::ctx_fail(ctx, EPHDC_EUNSUPPORTED,
-                           "the static-scratch path needs layout 0 and the full model");
+                           "the static-scratch path needs layout 0 and the full residue model");
 
   const size_t G = ((size_t)B + d.cap - 1) / d.cap;
   const size_t count = G * d.Kp;

@@ -84,6 +84,7 @@ _SIGS = {
     "ephdc_find_dmax_trial": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int32, _VP, _VP, _VP, _VP]),
     "ephdc_model_seeded_bytes": (ctypes.c_size_t, [_VP]),
     "bfv_model_to_seeded": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "bfv_model_to_digits": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "bfv_model_from_seeded": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64, _VP, _VP]),
 }
 
@@ -337,6 +338,14 @@ class Context:
         out = self._u32(lib().ephdc_model_seeded_bytes(self.ctx))
         _check(self.ctx, lib().bfv_model_to_seeded(self.ctx, _ptr(model, "model"),
                                                    _ptr(out, "seeded"), _stream(stream)))
+        return out
+
+    def model_to_digits(self, model, stream=None):
+        """The digit model (this context has "model_digits" 1) of a residue model in the
+        standard device order."""
+        out = self._u32(lib().ephdc_model_bytes(self.ctx))
+        _check(self.ctx, lib().bfv_model_to_digits(self.ctx, _ptr(model, "model"),
+                                                   _ptr(out, "model_digits"), _stream(stream)))
         return out
 
     def model_from_seeded(self, seeded, seed, stream=None):

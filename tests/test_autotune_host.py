@@ -1,0 +1,56 @@
+"""Host logic of the multiply-accumulate autotuner (no GPU): which schedules it offers
+for each storage form of the plaintexts and the model, so that it never times a
+schedule the context would refuse, and the cache key separates the forms."""
+import pytest
+
+from paper_2511_00737_gb300 import autotune as AT
+
+
+class FakeCtx:
+    """The knobs and sizes candidates() and _key() read."""
+
+    def __init__(self, Kp=16, layout=0, model_seed=-1, model_digits=0):
+        self.Kp, self.n, self.L, self.k, self.k_in, self.r, self.device = Kp, 8192, 4, Kp, 1, 8, 0
+        self.knobs = {"layout": layout, "model_seed": model_seed, "model_digits": model_digits}
+
+    def tune_get(self, k):
+        return self.knobs[k]
+
+
+def modes(cands):
+    return sorted({c["mac_mode"] for c in cands})
+
+
+def test_residue_model_offers_streaming_tiled_and_tensor_cores():
+    c = AT.candidates(FakeCtx(Kp=16), 64)
+    assert modes(c) == [1, 2, 3]
+    assert all("mac_cluster" not in k for k in c)
+    # a single group: no multi-group schedules
+    assert modes(AT.candidates(FakeCtx(Kp=16), 1)) == [1]
+    # more than 32 outputs: no tensor-core schedule
+    assert 3 not in modes(AT.candidates(FakeCtx(Kp=17), 64))
+
+
+def test_blocked_layout_offers_only_the_tensor_core_product():
+    assert AT.candidates(FakeCtx(layout=1), 64) == [{"mac_mode": 3}]
+
+
+def test_compact_model_offers_only_the_tiled_product():
+    assert modes(AT.candidates(FakeCtx(model_seed=7), 64)) == [2]
+    assert AT.candidates(FakeCtx(model_seed=7), 1) == [{"mac_mode": 2}]
+
+
+@pytest.mark.parametrize("G,clusters", [(1, [1]), (16, [1]), (17, [1, 2]), (32, [1, 2]),
+                                        (33, [1, 2, 4]), (64, [1, 2, 4]), (500, [1, 2, 4])])
+def test_digit_model_offers_the_digit_product_per_cluster_size(G, clusters):
+    c = AT.candidates(FakeCtx(model_digits=1), G)
+    assert modes(c) == [4]
+    # cluster sizes up to the power of two that covers the 16-group blocks
+    assert [k["mac_cluster"] for k in c] == clusters
+
+
+def test_cache_key_separates_storage_forms(monkeypatch):
+    monkeypatch.setattr(AT.torch.cuda, "get_device_name", lambda d: "GPU X")
+    keys = {AT._key(FakeCtx(**kw), 64) for kw in
+            ({}, {"layout": 1}, {"model_seed": 3}, {"model_digits": 1})}
+    assert len(keys) == 4
