@@ -58,7 +58,7 @@ constexpr int TCOLS = 512;
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 constexpr size_t SMEM = 1024 + NA * A_BYTES + NB * B_BYTES + NS * RAW_STEP + 256;
 constexpr long long WAIT_LIMIT = 1ll << 29;  // cycles (about a quarter of a second)
-static_assert(NB * B_BYTES >= 2 * 4 * 512 * 4, "the read-out staging lives in the B region");
+static_assert(NB * B_BYTES >= 2 * 4 * 512 * 8, "the read-out staging lives in the B region");
 static_assert(SMEM <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -234,12 +234,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int O = 2 * (int)c.Kp;
-  const uint32_t P = c.P, n = c.n, L = c.L;
-  const uint32_t l = blockIdx.z, kt = blockIdx.y, k0 = kt * KB;
-  const int g0 = blockIdx.x * GN;
-  const int steps = (int)((P + KC - 1) / KC);
+  const uint32_t P = c.P, n = c.n, L = c.L, nkt = n / KB;
+  const uint32_t S = (P + KC - 1) / KC;  // steps per tile
   const uint32_t CL = cluster_size(), rank = cluster_rank();
   const uint16_t cmask = (uint16_t)((1u << CL) - 1u);
+  // cluster tiles: (block of CL consecutive group blocks, 8 coefficients, limb); cluster
+  // cid takes cid, cid + NC, ...; this CTA the group block of its rank in each
+  const uint32_t GBC = ((G + GN - 1) / GN + CL - 1) / CL, NT = GBC * nkt * L;
+  const uint32_t cid = blockIdx.x / CL, NC = gridDim.x / CL;
+  const uint32_t T = cid < NT ? (NT - cid + NC - 1) / NC : 0;
+  const uint32_t TS = T * S;  // steps of all of this CTA's tiles
+  auto tile_of = [&](uint32_t tau, uint32_t& l, uint32_t& k0, int& g0) {
+    const uint32_t ct = cid + tau * NC, rest = ct / GBC;
+    g0 = (int)(((ct % GBC) * CL + rank) * GN);
+    k0 = (rest % nkt) * KB;
+    l = rest / nkt;
+  };
 
   if (tid == 0) {
     for (int b = 0; b < NA; b++) {
@@ -272,37 +282,48 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     // ------------------------------------------------------------ model producer
     if (lane == 0) {
       const uint32_t share = A_BYTES / CL;
-      const uint8_t* msrc = reinterpret_cast<const uint8_t*>(model) +
-                            ((size_t)l * (n / KB) + kt) * (size_t)steps * A_BYTES + rank * share;
-      for (int s = 0; s < steps && alive; s++) {
-        const int b = s % NA;
-        if (s >= NA && !mbar_wait(smem_u32(&mfree[b]), ((s / NA) - 1) & 1, status, 21)) {
+      const uint8_t* mbase = reinterpret_cast<const uint8_t*>(model) + rank * share;
+      uint32_t tau = 0, s = 0, l = 0, k0 = 0;
+      int g0 = 0;
+      tile_of(0, l, k0, g0);
+      for (uint32_t sg = 0; sg < TS && alive; sg++) {
+        const uint32_t b = sg % NA;
+        if (sg >= NA && !mbar_wait(smem_u32(&mfree[b]), ((sg / NA) - 1) & 1, status, 21)) {
           alive = false;
           break;
         }
         mbar_arrive_tx(smem_u32(&fullA[b]), A_BYTES);
-        bulk_copy(smem_u32(Areg + b * A_BYTES) + rank * share, msrc + (size_t)s * A_BYTES, share,
+        bulk_copy(smem_u32(Areg + b * A_BYTES) + rank * share,
+                  mbase + (((size_t)l * nkt + k0 / KB) * S + s) * A_BYTES, share,
                   smem_u32(&fullA[b]), cmask, CL > 1);
+        if (++s == S) {
+          s = 0;
+          tile_of(++tau, l, k0, g0);
+        }
       }
       // drain: every cluster CTA's MMAs of the last steps (and so every arrival on this
       // CTA's mfree barriers) are complete before the CTA may leave the cluster
-      for (int s = steps - NA < 0 ? 0 : steps - NA; s < steps && alive; s++)
-        if (!mbar_wait(smem_u32(&mfree[s % NA]), (s / NA) & 1, status, 22)) alive = false;
+      for (uint32_t sg = TS > NA ? TS - NA : 0; sg < TS && alive; sg++)
+        if (!mbar_wait(smem_u32(&mfree[sg % NA]), (sg / NA) & 1, status, 22)) alive = false;
     }
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      for (int s = 0; s < steps && alive; s++) {
-        const int a = s % NA, b = s % NB;
-        if (!mbar_wait(smem_u32(&fullA[a]), (s / NA) & 1, status, 23) ||
-            !mbar_wait(smem_u32(&fullB[b]), (s / NB) & 1, status, 27)) {
+      uint32_t s = 0, windows = 0;
+      for (uint32_t sg = 0; sg < TS && alive; sg++) {
+        const uint32_t a = sg % NA, b = sg % NB;
+        if (!mbar_wait(smem_u32(&fullA[a]), (sg / NA) & 1, status, 23) ||
+            !mbar_wait(smem_u32(&fullB[b]), (sg / NB) & 1, status, 27)) {
           alive = false;
           break;
         }
         const bool first = (s % WINS) == 0;
-        if (first && s > 0 && !mbar_wait(smem_u32(tfree), ((s / WINS) - 1) & 1, status, 24)) {
-          alive = false;
-          break;
+        if (first) {  // the previous window must have been read out of TMEM
+          if (windows > 0 && !mbar_wait(smem_u32(tfree), (windows - 1) & 1, status, 24)) {
+            alive = false;
+            break;
+          }
+          windows++;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         const uint32_t a0 = smem_u32(Areg + a * A_BYTES), b0 = smem_u32(Breg + b * B_BYTES);
@@ -313,6 +334,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
         if (CL > 1) tc_commit_mc(smem_u32(&mfree[a]), cmask);
         else tc_commit(smem_u32(&mfree[a]));
         tc_commit(smem_u32(&doneB[b]));
+        if (++s == S) s = 0;
       }
     }
   } else {
@@ -320,32 +342,52 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     // copies: 16-byte halves hh of pieces (g, i) (coefficients k0 + 4 hh .. + 3 of group
     // g0 + g, plaintext 16 s + i), two per thread, the two halves of a piece in adjacent
     // threads; slot (i * 16 + g) * 32 with the halves swapped when bit 2 of g is set, so
-    // that the split's 4-byte reads of a warp fall in 32 distinct banks
-    const uint32_t* src[2];
+    // that the split's 4-byte reads of a warp fall in 32 distinct banks.  The copies run
+    // NS - 1 steps ahead, across tile boundaries.
+    int cg[2], ci[2], chh[2];
     uint32_t dsto[2];
-    bool gok[2];
-    int pi[2];
 #pragma unroll
     for (int m = 0; m < 2; m++) {
-      const int cidx = tid + SPLITTERS * m, p = cidx >> 1, hh = cidx & 1;
-      const int g = p & 15, i = p >> 4;
-      gok[m] = g0 + g < G;
-      pi[m] = i;
-      src[m] = pt + ((size_t)(gok[m] ? g0 + g : 0) * P * L + l) * n + k0 + 4 * hh;
-      dsto[m] = (uint32_t)((i * 16 + g) * 32 + 16 * (hh ^ ((g >> 2) & 1)));
+      const int cidx = tid + SPLITTERS * m, pc = cidx >> 1;
+      chh[m] = cidx & 1;
+      cg[m] = pc & 15;
+      ci[m] = pc >> 4;
+      dsto[m] = (uint32_t)((ci[m] * 16 + cg[m]) * 32 + 16 * (chh[m] ^ ((cg[m] >> 2) & 1)));
     }
     const size_t pstride = (size_t)L * n;  // words between plaintexts of a group
-    auto issue = [&](int s) {
-      if (s < steps && alive) {
-        const uint32_t base = smem_u32(ring + (s % NS) * RAW_STEP);
+    uint32_t isg = 0, is = 0, itau = 0;    // next step to copy, its step in its tile, tile
+    const uint32_t* isrc[2];
+    bool igok[2];
+    auto issue_tile = [&]() {
+      uint32_t l, k0;
+      int g0;
+      tile_of(itau, l, k0, g0);
+#pragma unroll
+      for (int m = 0; m < 2; m++) {
+        igok[m] = g0 + cg[m] < G;
+        isrc[m] = pt + ((size_t)(igok[m] ? g0 + cg[m] : 0) * P * L + l) * n + k0 + 4 * chh[m];
+      }
+    };
+    issue_tile();
+    auto issue = [&]() {
+      if (isg < TS && alive) {
+        const uint32_t base = smem_u32(ring + (isg % NS) * RAW_STEP);
 #pragma unroll
         for (int m = 0; m < 2; m++) {
-          const uint32_t i = (uint32_t)(s * KC + pi[m]);
-          const bool ok = gok[m] && i < P;
-          cp_async16(base + dsto[m], ok ? src[m] + (size_t)i * pstride : pt, ok);
+          const uint32_t i = is * KC + (uint32_t)ci[m];
+          const bool ok = igok[m] && i < P;
+          cp_async16(base + dsto[m], ok ? isrc[m] + (size_t)i * pstride : pt, ok);
         }
       }
       asm volatile("cp.async.commit_group;\n" ::: "memory");
+      if (isg < TS) {
+        isg++;
+        if (++is == S) {
+          is = 0;
+          itau++;
+          if (isg < TS) issue_tile();
+        }
+      }
     };
     // split: coefficient j of pieces (g, 8 h + e), e < 8 -> B rows 16 u + g, columns
     // 8 h .. 8 h + 7 of coefficient j's operand (one 16-byte store per digit u)
@@ -353,8 +395,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     const int sj = ((lane >> 3) & 3) | (((warp >> 2) & 1) << 2);
     const int sh = (warp >> 1) & 1;
     const uint32_t roff = (uint32_t)(sg * 32 + 16 * ((sj >> 2) ^ ((sg >> 2) & 1)) + 4 * (sj & 3));
-    auto split = [&](int s, int buf) {
-      const uint8_t* R = ring + (s % NS) * RAW_STEP + roff;
+    auto split = [&](uint32_t step, int buf) {
+      const uint8_t* R = ring + (step % NS) * RAW_STEP + roff;
       uint32_t x[8];
 #pragma unroll
       for (int e = 0; e < 8; e++)
@@ -371,23 +413,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     uint32_t acc[KB][2];
 #pragma unroll
     for (int j = 0; j < KB; j++) acc[j][0] = acc[j][1] = 0;
-    uint32_t* stage = reinterpret_cast<uint32_t*>(Breg);  // [2 jj][4 v][16 g][32 o]
-    const ModP m = c.mq[l];
+    int64_t* stage = reinterpret_cast<int64_t*>(Breg);  // [2 jj][4 v][16 g][32 o]
     // read-out: warp w reads TMEM lanes 32 v + o (v = w % 4, output o = lane) of
     // coefficients 2 p + w / 4, weighting the sum of digit pair (u, v) by 2^(8(u+v))
     const int qv = warp & 3, jj = warp >> 2;
+    uint32_t tl = 0, tk0 = 0;  // the tile being accumulated
+    int tg0 = 0;
+    ModP m;
     uint32_t W[4];
-    {
+    uint64_t OFF = 0;
+    auto start_tile = [&](uint32_t tau) {
+      tile_of(tau, tl, tk0, tg0);
+      m = c.mq[tl < L ? tl : 0];
       uint32_t w = 1;
       for (int s = 0; s < qv; s++) w = mulm(w, 256u, m);
       for (int u = 0; u < 4; u++) {
         W[u] = w;
         w = mulm(w, 256u, m);
       }
-    }
-    // |sum_u W S| < 4 q 2^24 < 2^56: adding a multiple of q_l above 2^56 keeps it
-    // non-negative
-    const uint64_t OFF = ((1ull << 56) / m.p + 1) * m.p;
+      // |sum_{u,v} W S| < 16 q 2^24 < 2^58: adding a multiple of q_l above 2^58 keeps it
+      // non-negative (and below 2^60)
+      OFF = ((1ull << 58) / m.p + 1) * m.p;
+    };
     auto readout = [&]() {
 #pragma unroll
       for (int p = 0; p < KB / 2; p++) {
@@ -395,61 +442,71 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
         int64_t t[16];
 #pragma unroll
         for (int g = 0; g < 16; g++) t[g] = 0;
-        uint32_t S[64];  // column 16 u + g: digit pair (u, v), group g
-        tc_ld64(tmem + ((uint32_t)(32 * qv) << 16) + (uint32_t)(j * 64), S);
+        uint32_t Sv[64];  // column 16 u + g: digit pair (u, v), group g
+        tc_ld64(tmem + ((uint32_t)(32 * qv) << 16) + (uint32_t)(j * 64), Sv);
 #pragma unroll
         for (int u = 0; u < 4; u++)
 #pragma unroll
           for (int g = 0; g < 16; g++)
-            t[g] += (int64_t)__float2int_rn(__uint_as_float(S[16 * u + g])) * (int64_t)(int32_t)W[u];
+            t[g] += (int64_t)__float2int_rn(__uint_as_float(Sv[16 * u + g])) *
+                    (int64_t)(int32_t)W[u];
 #pragma unroll
-        for (int g = 0; g < 16; g++)
-          stage[(jj * 4 + qv) * 512 + g * 32 + lane] = red64((uint64_t)t[g] + OFF, m.p, m.mu);
+        for (int g = 0; g < 16; g++) stage[(jj * 4 + qv) * 512 + g * 32 + lane] = t[g];
         splitters_sync();
+        // sum over v of the exact partial sums (|.| < 2^58), made non-negative with a
+        // multiple of q_l above 2^58, and one reduction
 #pragma unroll
         for (int mm = 0; mm < 2; mm++)
 #pragma unroll
           for (int j2 = 0; j2 < 2; j2++) {
-            const uint32_t* st = stage + j2 * 4 * 512 + tid + SPLITTERS * mm;
-            const uint64_t v = (uint64_t)acc[2 * p + j2][mm] + st[0] + st[512] + st[1024] + st[1536];
-            acc[2 * p + j2][mm] = red64(v, m.p, m.mu);
+            const int64_t* st = stage + j2 * 4 * 512 + tid + SPLITTERS * mm;
+            const uint64_t v = (uint64_t)(st[0] + st[512] + st[1024] + st[1536]) + OFF;
+            acc[2 * p + j2][mm] = addm(acc[2 * p + j2][mm], red64(v, m.p, m.mu), m.p);
           }
         splitters_sync();
       }
     };
 
-    for (int s = 0; s < NS - 1; s++) issue(s);
+    for (int k = 0; k < NS - 1; k++) issue();
+    start_tile(0);
+    uint32_t s = 0, tau = 0;
 #pragma unroll 1
-    for (int s = 0; s < steps; s++) {
-      const int b = s % NB;
+    for (uint32_t sgl = 0; sgl < TS; sgl++) {
+      const int b = (int)(sgl % NB);
       asm volatile("cp.async.wait_group %0;\n" ::"n"(NS - 2) : "memory");
-      splitters_sync();  // every thread's pieces of step s have landed
-      issue(s + NS - 1);
-      // the buffer's previous MMAs (step s - NB) must be done before it is rewritten
-      if (s >= NB && alive &&
-          !mbar_wait(smem_u32(&doneB[b]), ((s / NB) - 1) & 1, status, 25))
+      splitters_sync();  // every thread's pieces of this step have landed
+      issue();
+      // the buffer's previous MMAs (step sgl - NB) must be done before it is rewritten
+      if (sgl >= NB && alive &&
+          !mbar_wait(smem_u32(&doneB[b]), ((sgl / NB) - 1) & 1, status, 25))
         alive = false;
-      if (alive) split(s, b);
+      if (alive) split(sgl, b);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       mbar_arrive(smem_u32(&fullB[b]));
-      if ((s % WINS) == WINS - 1 || s == steps - 1) {
-        const bool ok = alive && mbar_wait(smem_u32(&doneB[b]), (s / NB) & 1, status, 26);
+      if ((s % WINS) == WINS - 1 || s == S - 1) {
+        const bool ok = alive && mbar_wait(smem_u32(&doneB[b]), (sgl / NB) & 1, status, 26);
         alive = splitters_and(ok);
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         if (alive) readout();
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         mbar_arrive(smem_u32(tfree));
       }
-    }
-    // the 8 consecutive coefficients of (group, output) as two 16-byte stores
+      if (++s == S) {
+        // the tile's 8 consecutive coefficients of (group, output): two 16-byte stores
 #pragma unroll
-    for (int mm = 0; mm < 2; mm++) {
-      const int pair = tid + SPLITTERS * mm, g = pair >> 5, o = pair & 31;
-      if (alive && g0 + g < G && o < O) {
-        uint4* dst =
-            reinterpret_cast<uint4*>(out + (((size_t)(g0 + g) * O + o) * L + l) * n + k0);
-        dst[0] = make_uint4(acc[0][mm], acc[1][mm], acc[2][mm], acc[3][mm]);
-        dst[1] = make_uint4(acc[4][mm], acc[5][mm], acc[6][mm], acc[7][mm]);
+        for (int mm = 0; mm < 2; mm++) {
+          const int pair = tid + SPLITTERS * mm, g = pair >> 5, o = pair & 31;
+          if (alive && tg0 + g < G && o < O) {
+            uint4* dst = reinterpret_cast<uint4*>(
+                out + (((size_t)(tg0 + g) * O + o) * L + tl) * n + tk0);
+            dst[0] = make_uint4(acc[0][mm], acc[1][mm], acc[2][mm], acc[3][mm]);
+            dst[1] = make_uint4(acc[4][mm], acc[5][mm], acc[6][mm], acc[7][mm]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < KB; j++) acc[j][0] = acc[j][1] = 0;
+        s = 0;
+        if (++tau < T) start_tile(tau);
       }
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -481,18 +538,30 @@ cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint
   int cl = cluster > 0 ? cluster : 4;
   if (cl & (cl - 1) || cl > 8) return cudaErrorInvalidValue;
   if (cl > cover) cl = cover;
+  // persistent: as many clusters as are resident at once, each walking its tiles
+  const long long tiles = (long long)((gb + cl - 1) / cl) * (c.n / KB) * c.L;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(((gb + cl - 1) / cl) * cl), c.n / KB, c.L);
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = SMEM;
-  cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)cl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM;
+  cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)cl);
+  int resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, k_mac_uv, &cfg) != cudaSuccess || resident < 1) {
+    cudaGetLastError();
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    resident = sms / cl > 0 ? sms / cl : 1;
+  }
+  const long long nc = tiles < resident ? tiles : resident;
+  cfg.gridDim = dim3((unsigned)(nc * cl));
   return cudaLaunchKernelEx(&cfg, k_mac_uv, c, pt, model, acc, G, c.status);
 }
 
