@@ -163,10 +163,10 @@ ephdc_status bfv_ptct_similarity(ephdc_ctx* ctx, const uint32_t* pt_dev, int32_t
  *    library as a __device__ variable, which every GPU that loads the library holds
  *    until the process exits.  The context must still be created beforehand (that
  *    call allocates the context's tables).
- *  - The first call on a device looks up the array's device address (with that
- *    device current) and keeps it for the life of the process; make that first call
- *    before any stream capture, and do not use this entry point on a device after a
- *    cudaDeviceReset of it (the module, and with it the array, is loaded anew).
+ *  - Every call looks up the array's device address on the current device (a host
+ *    query, so it stays valid when a cudaDeviceReset loads the module anew); the
+ *    first call on a device may load the module, so make it before any stream
+ *    capture.
  *  - All calls share the one array, and it keeps the last call's contents (nothing
  *    in it needs to start at zero).  Calls whose work overlaps on the GPU -- on
  *    different streams, or from different contexts on the same device -- race on

@@ -3,7 +3,6 @@
 // device memory at run time (see include/ephdc.h).  It launches the same kernels as
 // bfv_ptct_similarity; only the location of the scratch differs.
 #include <cstdio>
-#include <mutex>
 
 #include "ephdc_internal.cuh"
 
@@ -14,21 +13,16 @@ static __device__ __align__(256) uint32_t g_static_scratch[EPHDC_STATIC_SCRATCH_
 namespace {
 
 constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-uint32_t* g_scratch_dev[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device, looked up once per
-// device.  In host code the symbol only names a host-side stand-in, so kernels must
-// be given this address, never &g_static_scratch.
-cudaError_t scratch_address(int device, uint32_t** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_dev[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_dev[device] = static_cast<uint32_t*>(p);
-  }
-  *out = g_scratch_dev[device];
+// Device address of g_static_scratch on the current device.  In host code the symbol
+// only names a host-side stand-in, so kernels must be given this address, never
+// &g_static_scratch.  Looked up on every call (a host-side query), so that it stays
+// valid when the module is loaded anew after a cudaDeviceReset.
+cudaError_t scratch_address(uint32_t** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<uint32_t*>(p);
   return cudaSuccess;
 }
 
@@ -71,7 +65,7 @@ extern "C" ephdc_status bfv_ptct_similarity_noalloc(ephdc_ctx* ctx, const uint32
   if (dev != ephdc::ctx_device(ctx))
     return ephdc::ctx_fail(ctx, EPHDC_EINVAL, "the current device is not the context's device");
   uint32_t* base = nullptr;
-  cudaError_t e = scratch_address(dev, &base);
+  cudaError_t e = scratch_address(&base);
   if (e != cudaSuccess) return ephdc::ctx_fail(ctx, EPHDC_ECUDA, cudaGetErrorString(e));
 
   // layout: acc | tmp | digits | partial sums (as many splits as fit)
