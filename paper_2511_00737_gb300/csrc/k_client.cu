@@ -422,32 +422,33 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
     xr[r] = r < R ? cluster.map_shared_rank(x, r) : x;
     kr[r] = gkj + ((size_t)(r < l ? r : r + 1) * L + l) * 4 * N;
   }
+  // the products accumulate in 64 bits: every factor is below q_l < 2^30, so the L
+  // products (< 2^60 each) and the two added words stay below 2^63 and are reduced
+  // once; only the key parts k0, k1 are read (not their Shoup quotients)
   for (uint32_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const uint32_t gp = galois_pos(j, gal, LOGN);
     uint64_t s0 = (uint64_t)__ldg(&c0[j]) + __ldg(&c0[gp]);
     uint64_t s1 = __ldg(&c1[j]);
     // every rank's loads issued before the first product (L is at most EPHDC_MAXL)
     const uint32_t vl = __ldg(&c1[gp]);
-    const uint4 kvl = make_uint4(__ldg(kl + j), __ldg(kl + N + j), __ldg(kl + 2 * N + j),
-                                 __ldg(kl + 3 * N + j));
-    uint32_t v[EPHDC_MAXL - 1];
-    uint4 kv[EPHDC_MAXL - 1];
+    const uint32_t k0l = __ldg(kl + j), k1l = __ldg(kl + 2 * N + j);
+    uint32_t v[EPHDC_MAXL - 1], k0[EPHDC_MAXL - 1], k1[EPHDC_MAXL - 1];
     const uint32_t pj = padi(j);
 #pragma unroll
     for (uint32_t r = 0; r < EPHDC_MAXL - 1; r++) {
       if (r < R) {
         v[r] = xr[r][pj];
-        const uint32_t* k = kr[r] + j;
-        kv[r] = make_uint4(__ldg(k), __ldg(k + N), __ldg(k + 2 * N), __ldg(k + 3 * N));
+        k0[r] = __ldg(kr[r] + j);
+        k1[r] = __ldg(kr[r] + 2 * N + j);
       }
     }
-    s0 += mulshoup(vl, kvl.x, kvl.y, p);  // each term < 2p
-    s1 += mulshoup(vl, kvl.z, kvl.w, p);
+    s0 += (uint64_t)vl * k0l;
+    s1 += (uint64_t)vl * k1l;
 #pragma unroll
     for (uint32_t r = 0; r < EPHDC_MAXL - 1; r++) {
       if (r < R) {
-        s0 += mulshoup(v[r], kv[r].x, kv[r].y, p);
-        s1 += mulshoup(v[r], kv[r].z, kv[r].w, p);
+        s0 += (uint64_t)v[r] * k0[r];
+        s1 += (uint64_t)v[r] * k1[r];
       }
     }
     o0[j] = red64(s0, p, m.mu);
