@@ -33,19 +33,44 @@ struct CentredLift {
     return v <= thalf ? v : v + p_minus_t;
   }
 };
+// the same lift from the compact copy of the coefficients: the centred value c in
+// [-32768, 32768] as int16 (padded index), except c = 32768, which int16 cannot hold:
+// stored as 0 with its bit set in `big` (one bit per padded index)
+struct CompactLift {
+  static constexpr bool kPadded = true;
+  const int16_t* s;
+  const uint32_t* big;
+  uint32_t p;
+  __device__ __forceinline__ uint32_t at(uint32_t pi) const {
+    const int c = s[pi];
+    const uint32_t v = c < 0 ? (uint32_t)(c + (int)p) : (uint32_t)c;
+    return (big[pi >> 5] >> (pi & 31)) & 1u ? 32768u : v;
+  }
+};
+// shared memory of the encoder: two padded u32 buffers, or (n = 16384, so that two
+// CTAs fit on an SM) one u32 buffer plus the compact coefficient copy
+__host__ __device__ constexpr size_t encode_smem_bytes(uint32_t logn) {
+  return logn >= 14 ? padded_words(1u << logn) * 4 + padded_words(1u << logn) * 2 +
+                          (padded_words(1u << logn) / 32 + 1) * 4
+                    : 2 * (size_t)padded_words(1u << logn) * 4;
+}
 
 // One CTA per plaintext (g, i).  The query slots are packed (pack_query_slots), the
 // inverse NTT mod t gives the plaintext coefficients, and for each limb the centred
 // lift feeds the forward NTT, whose output is staged in shared memory and stored
 // with 16-byte writes.  (The scaling operation, when on, is a separate pass.)
 template <int LOGN, int V>
-__global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
+__global__ void __launch_bounds__(256, LOGN >= 14 ? 2 : 3)
     k_encode_plain(DevCtx c, const int8_t* __restrict__ H, int B, uint32_t* __restrict__ pt,
                    uint32_t i0, uint32_t ni) {
   constexpr uint32_t N = 1u << LOGN;
+  constexpr bool CPT = LOGN >= 14;  // compact coefficient copy
   extern __shared__ uint32_t sm[];
-  uint32_t* mb = sm;
-  uint32_t* wb = sm + padded_words(N);
+  uint32_t* wb = sm;
+  // the coefficients mod t: a second u32 buffer, or the compact copy filled from wb
+  uint32_t* mb = CPT ? wb : sm + padded_words(N);
+  int16_t* m16 = reinterpret_cast<int16_t*>(sm + padded_words(N));
+  uint32_t* big = reinterpret_cast<uint32_t*>(m16 + padded_words(N));
   // block gi: plaintext i0 + gi % ni of group gi / ni, stored as plaintext gi of a
   // buffer of ni plaintexts per group (the whole pass: i0 = 0, ni = P)
   const uint32_t gi = blockIdx.x;
@@ -64,10 +89,25 @@ __global__ void __launch_bounds__(LOGN >= 14 ? 512 : 256, LOGN >= 14 ? 1 : 3)
   if (c.t == 65537u) ntt_inv_t<LOGN, V, false, true>(mb, c.mt);
   else ntt_inv_t<LOGN, V, false>(mb, c.mt);
   const uint32_t t = c.t, thalf = (t - 1) / 2;
+  if (CPT) {  // wb -> the compact copy (centred values; 32768 flagged)
+    for (uint32_t w = threadIdx.x; w < padded_words(N) / 32 + 1; w += blockDim.x) big[w] = 0;
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+      const uint32_t pi = padi(k), v = wb[pi];
+      const int cv = v <= thalf ? (int)v : (int)v - (int)t;
+      if (cv == 32768) atomicOr(&big[pi >> 5], 1u << (pi & 31));
+      m16[pi] = (int16_t)(cv == 32768 ? 0 : cv);
+    }
+    __syncthreads();
+  }
   for (uint32_t l = 0; l < c.L; l++) {
     const ModP m = c.mq[l];
-    const CentredLift lift{mb, thalf, m.p - t};
-    ntt_fwd_io<LOGN, CentredLift, SmemSt, V>(wb, m, lift, SmemSt{wb});
+    if constexpr (CPT) {
+      ntt_fwd_io<LOGN, CompactLift, SmemSt, V>(wb, m, CompactLift{m16, big, m.p}, SmemSt{wb});
+    } else {
+      const CentredLift lift{mb, thalf, m.p - t};
+      ntt_fwd_io<LOGN, CentredLift, SmemSt, V>(wb, m, lift, SmemSt{wb});
+    }
     if (c.layout) {  // coefficient-blocked: 16 bytes per (coefficient block, g, i)
       const uint32_t G = ((uint32_t)B + c.cap - 1) / c.cap;
       uint4* dst = reinterpret_cast<uint4*>(pt);
@@ -500,13 +540,15 @@ cudaError_t launch_encode_plain(const DevCtx& c, const int8_t* H, int B, uint32_
     ni = c.P;
   }
   if (ni != c.P && (c.layout || c.scale_g)) return cudaErrorNotSupported;
-  const size_t smem = 2 * padded_words(c.n) * sizeof(uint32_t);
+  const size_t smem = encode_smem_bytes(c.logn);
+  // at most 256 threads: at n = 16384 two CTAs per SM (compact coefficient copy)
+  const unsigned threads = ntt_threads(c) < 256 ? ntt_threads(c) : 256;
   EPHDC_DISPATCH_LOGN(c.logn, LG, {
     auto kern = c.ntt_plan == 1 ? k_encode_plain<LG, 1>
               : c.ntt_plan == 2 ? k_encode_plain<LG, 2> : k_encode_plain<LG, 0>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<G * ni, ntt_threads(c), smem, st>>>(c, H, B, pt, i0, ni);
+    kern<<<G * ni, threads, smem, st>>>(c, H, B, pt, i0, ni);
   });
   if (c.scale_g) k_scale_plain<<<G * c.P, 256, 0, st>>>(c, pt);
   return cudaGetLastError();
