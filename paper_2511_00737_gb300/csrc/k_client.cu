@@ -384,6 +384,9 @@ __global__ void k_mac_reduce(DevCtx c, const uint32_t* __restrict__ partial, int
 // (80 registers) at n = 8192, two (128 registers) at n = 16384, where the transform
 // passes need more; smaller rings launch fewer threads and need no bound
 constexpr int ks_min_blocks(int logn) { return logn == 13 ? 3 : logn >= 14 ? 2 : 1; }
+// pass schedule of the key-switch and export transforms: radix-32 passes last (the
+// schedule the encoder's autotuner picks at n = 8192 and 16384)
+constexpr int KS_PLAN = 2;
 
 // digits[ct][i][:] = tau_g(INTT_{q_i}(c1 limb i)): the RNS digits of the rotated c1 as
 // integer polynomials with coefficients in [0, q_i).  The automorphism X -> X^g is
@@ -409,12 +412,12 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
     w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
   }
   __syncthreads();
-  ntt_inv_io<LOGN>(sm, c.mq[i], SmemLd{sm},
-                   [=](uint32_t k, uint32_t v) {
-                     const uint32_t e = (k * gal) & (2 * N - 1);
-                     if (e < N) dst[e] = v;
-                     else dst[e - N] = v ? q - v : 0;
-                   });
+  const auto st = [=](uint32_t k, uint32_t v) {
+    const uint32_t e = (k * gal) & (2 * N - 1);
+    if (e < N) dst[e] = v;
+    else dst[e - N] = v ? q - v : 0;
+  };
+  ntt_inv_io<LOGN, SmemLd, decltype(st), KS_PLAN>(sm, c.mq[i], SmemLd{sm}, st);
 }
 
 // Key switch and add, one thread-block cluster of L - 1 CTAs per (ciphertext, target
@@ -444,8 +447,8 @@ __global__ void __launch_bounds__(256, ks_min_blocks(LOGN))
   {
     const uint32_t d = i < l ? i : i + 1;
     const uint32_t* dg = digits + ((size_t)ct * c.L + d) * N;
-    ntt_fwd_io<LOGN>(x, m, [=](uint32_t kk) { return csub(__ldg(&dg[kk]), p); },  // d < 2 q_l
-                     SmemSt{x});
+    const auto ld = [=](uint32_t kk) { return csub(__ldg(&dg[kk]), p); };  // d < 2 q_l
+    ntt_fwd_io<LOGN, decltype(ld), SmemSt, KS_PLAN>(x, m, ld, SmemSt{x});
   }
   cluster.sync();
   const uint32_t slice = (N + R - 1) / R;
@@ -515,7 +518,8 @@ __global__ void __launch_bounds__(512) k_export(DevCtx c, const uint32_t* __rest
     w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
   }
   __syncthreads();
-  ntt_inv_io<LOGN>(sm, c.mq[l], SmemLd{sm}, [=](uint32_t k, uint32_t v) { dst[k] = v; });
+  const auto st = [=](uint32_t k, uint32_t v) { dst[k] = v; };
+  ntt_inv_io<LOGN, SmemLd, decltype(st), KS_PLAN>(sm, c.mq[l], SmemLd{sm}, st);
 }
 
 inline unsigned ntt_threads(const DevCtx& c) {
