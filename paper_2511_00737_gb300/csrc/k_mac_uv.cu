@@ -16,22 +16,23 @@
 // The model is stored already split (the digit model: for every limb, 8 coefficients
 // and 16 plaintexts, the 8 fp16 A operands of 128 rows x 16 columns, 4 KB each, in the
 // order mdig_index gives), so a step's model operand is one contiguous 32 KB block
-// copied into shared memory by the bulk-copy engine; the CTAs of a cluster (consecutive group blocks of the same coefficients)
-// each copy a share of it and multicast it to all of them.  Plaintexts stay in the
-// standard layout and arrive as 32-byte pieces (8 coefficients of one (group,
-// plaintext) row) through cp.async.
+// copied into shared memory by the bulk-copy engine; the CTAs of a cluster
+// (consecutive group blocks of the same coefficients) each copy a share of it and
+// multicast it to all of them.  Plaintexts stay in the standard layout and arrive as
+// 32-byte pieces (8 coefficients of one (group, plaintext) row) through cp.async.
 //
-// One CTA per tile (limb l, 8 consecutive coefficients, 16 groups; all outputs O <= 32,
-// all plaintexts) with three kinds of warps: 8 splitter warps copy the plaintext pieces
-// of the step NS - 1 ahead, split the current step into digits (B operand) and arrive
-// on the buffer's "full" mbarrier; one producer thread copies the model operand of the
-// step (its expect-tx arrival completes "full" with the bytes); one MMA thread waits for
-// "full", issues the step's 8 MMAs and commits to the buffer's local "done" barrier and
-// to the "mfree" barrier of every CTA of the cluster (a buffer's model operand is
-// rewritten only after every CTA's MMAs of the step that used it are complete).  The 8
-// accumulators (128 lanes x 64 columns each) fill all 512 TMEM columns.  All waits are
-// bounded; a CTA that gave up records the code, stops issuing work and still takes part
-// in the cluster barriers.
+// A tile is (limb l, 8 consecutive coefficients, 16 groups; all outputs O <= 32, all
+// plaintexts).  Persistent CTAs (clusters) walk their tiles with three kinds of warps:
+// 8 splitter warps copy the plaintext pieces NS - 1 steps ahead (across tile
+// boundaries), split the current step into digits (B operand, "fullB" mbarrier) and
+// read each window out of TMEM; one producer thread bulk-copies the model operand NA
+// steps ahead (its expect-tx arrival and the bytes complete "fullA"); one MMA thread
+// waits for both, issues the step's 8 MMAs and commits to the digit buffer's local
+// "doneB" barrier and to the model buffer's "mfree" barrier in every CTA of the
+// cluster (a model buffer is rewritten only after every CTA's MMAs that read it are
+// complete).  The 8 accumulators (128 lanes x 64 columns each) fill all 512 TMEM
+// columns.  All waits are bounded; a CTA that gave up records the code, stops issuing
+// work and still takes part in the cluster barriers.
 #include <cuda_fp16.h>
 
 #include "ephdc_internal.cuh"
@@ -517,6 +518,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "n"(TCOLS)
                  : "memory");
+  // after a recorded failure some waits were skipped: give copies and commits already
+  // issued (by this CTA or a peer) 50 us to land before the CTAs leave the cluster
+  if (tid == 0 && *(volatile uint32_t*)status != 0u) {
+    const long long t0 = clock64();
+    while (clock64() - t0 < 100000ll) __nanosleep(1000);
+  }
   cluster_sync();  // no CTA leaves while a peer may still signal or fill it
 }
 
