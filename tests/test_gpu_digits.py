@@ -53,6 +53,7 @@ LAYOUTS = [
     (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 0),     # G = 70: clusters of 4, 3 CTAs without groups
     (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 1),     # the same without clusters
     (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 2),     # clusters of 2
+    (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 8),     # one cluster of 8 (3 CTAs without groups)
 ]
 
 
