@@ -707,7 +707,7 @@ def per_query_form(w, dev, queries=32):
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of
 # the same kernel and launch shape (dram__bytes_read.sum + dram__bytes_write.sum):
 # (workload, groups per launch, stage) -> bytes
-NCU_TRAFFIC = {("face1024", 16, "encode_plain"): 2724355712}
+NCU_TRAFFIC = {("face1024", 16, "encode_plain"): 2727000320}
 
 
 def roofline(ctx, w, B, dom, stage_ms, stage_calls, pk, src):
