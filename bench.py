@@ -906,7 +906,14 @@ def run_legs(args):
         a.compact = chunk < 0   # the compact-model leg
         w = WL.config(wname)
         t0 = time.perf_counter()
-        line = run_serve(a, w) if wname == "serve" else run_ours(a, w, w.B)
+        try:
+            line = run_serve(a, w) if wname == "serve" else run_ours(a, w, w.B)
+        except Exception as ex:  # a failed leg is reported; the headline line still prints
+            import traceback
+            traceback.print_exc(file=sys.stderr)
+            out[name] = {"error": "%s: %s" % (type(ex).__name__, str(ex)[:300]),
+                         "wall_s": time.perf_counter() - t0}
+            continue
         rec = {k: line[k] for k in LEG_KEYS if k in line}
         rec["wall_s"] = time.perf_counter() - t0
         if name == "serve":
