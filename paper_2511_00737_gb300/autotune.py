@@ -100,11 +100,19 @@ def tune_similarity(ctx, pt, B, model, gk, reps=5, use_cache=True, max_candidate
     cands = candidates(ctx, G)
     if max_candidates:
         cands = cands[:max_candidates]
+    from .ephdc import EphdcError
     for knobs in cands:
         base = {"mac_mode": 0, "mac_splits": 0}
-        apply(ctx, {**base, **knobs})
-        ms = _time(lambda: ctx.ptct_similarity_into(pt, B, model, gk, out), reps)
+        try:
+            apply(ctx, {**base, **knobs})
+            ms = _time(lambda: ctx.ptct_similarity_into(pt, B, model, gk, out), reps)
+        except EphdcError:
+            # a schedule this device refuses to launch (a cluster it cannot place, a
+            # tile over its shared memory) is skipped; the others are still timed
+            continue
         table.append((ms, knobs))
+    if not table:
+        raise RuntimeError("no multiply-accumulate schedule could be launched")
     table.sort(key=lambda x: x[0])
     best_ms, best = table[0]
     apply(ctx, {"mac_mode": 0, "mac_splits": 0, **best})

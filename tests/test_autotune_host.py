@@ -54,3 +54,43 @@ def test_cache_key_separates_storage_forms(monkeypatch):
     keys = {AT._key(FakeCtx(**kw), 64) for kw in
             ({}, {"layout": 1}, {"model_seed": 3}, {"model_digits": 1})}
     assert len(keys) == 4
+
+
+def test_tuner_skips_schedules_the_device_refuses(monkeypatch):
+    """A candidate whose launch fails (EphdcError, e.g. a cluster shape the device cannot
+    place) is skipped and the fastest of the others is applied; if none runs, it says so."""
+    from paper_2511_00737_gb300.ephdc import EphdcError
+
+    class TunableCtx(FakeCtx):
+        def __init__(self, refuse):
+            super().__init__(model_digits=1)
+            self.refuse, self.set = refuse, {}
+
+        def groups(self, B):
+            return B
+
+        def out_ct(self, B):
+            return None
+
+        def tune_set(self, k, v):
+            self.set[k] = v
+
+        def ptct_similarity_into(self, *a):
+            if self.set.get("mac_cluster") in self.refuse:
+                raise EphdcError("EPHDC_ECUDA: cluster cannot be placed")
+
+    # time = cluster size: the refused cluster 1 would have been the fastest
+    def timed(fn, reps):
+        fn()
+        return {1: 1.0, 2: 2.0, 4: 4.0}[ctx.set["mac_cluster"]]
+
+    monkeypatch.setattr(AT, "_time", timed)
+    monkeypatch.setattr(AT.torch.cuda, "get_device_name", lambda d: "GPU X")
+    ctx = TunableCtx(refuse={1})
+    best, ms, table = AT.tune_similarity(ctx, None, 64, None, None, use_cache=False)
+    assert best == {"mac_mode": 4, "mac_cluster": 2} and ms == 2.0
+    assert [k["mac_cluster"] for _, k in table] == [2, 4]
+    assert ctx.set["mac_cluster"] == 2   # the winner is applied last
+    ctx = TunableCtx(refuse={1, 2, 4})
+    with pytest.raises(RuntimeError, match="no multiply-accumulate schedule"):
+        AT.tune_similarity(ctx, None, 64, None, None, use_cache=False)
