@@ -77,7 +77,7 @@ def test_tuner_skips_schedules_the_device_refuses(monkeypatch):
 
         def ptct_similarity_into(self, *a):
             if self.set.get("mac_cluster") in self.refuse:
-                raise EphdcError("EPHDC_ECUDA: cluster cannot be placed")
+                raise EphdcError(-4, "cluster cannot be placed")
 
     # time = cluster size: the refused cluster 1 would have been the fastest
     def timed(fn, reps):
