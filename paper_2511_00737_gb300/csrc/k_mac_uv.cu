@@ -559,13 +559,22 @@ cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.gridDim = dim3((unsigned)cl);
-  int resident = 0;
-  if (cudaOccupancyMaxActiveClusters(&resident, k_mac_uv, &cfg) != cudaSuccess || resident < 1) {
-    cudaGetLastError();
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    resident = sms / cl > 0 ? sms / cl : 1;
+  // resident clusters per device and cluster size, asked once (a host-side query)
+  static int resident_cache[64][4];
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int ci = cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : 3;
+  int resident = dev < 64 ? resident_cache[dev][ci] : 0;
+  if (resident < 1) {
+    if (cudaOccupancyMaxActiveClusters(&resident, k_mac_uv, &cfg) != cudaSuccess ||
+        resident < 1) {
+      cudaGetLastError();
+      int sms = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      resident = sms / cl > 0 ? sms / cl : 1;
+    }
+    if (dev < 64) resident_cache[dev][ci] = resident;
   }
   const long long nc = tiles < resident ? tiles : resident;
   cfg.gridDim = dim3((unsigned)(nc * cl));
