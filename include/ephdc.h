@@ -318,11 +318,12 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * model): the model is stored as the fp16 tensor-core operand of the signed base-256
  * digits d_v of every residue (x = sum_{v<4} d_v 2^(8v), d_v = byte v of x + 0x80808080
  * less 128, |d_v| <= 128), so that the multiply-accumulate copies it into shared memory
- * without splitting it; ephdc_model_bytes = L n ceil(P/16) 4096 (twice the residue
- * model at k/k_in = 16).  Order: fp16 tiles of 128 rows x 16 columns, tile
- * ((l (n/8) + x/8) ceil(P/16) + i/16) 8 + x%8 for coefficient x of limb l and plaintext
- * i; row 32 v + o, column i%16 at byte (row/8) 256 + (column/8) 128 + (row%8) 16 +
- * (column%8) 2; rows of outputs o >= 2 k/k_in and columns of plaintexts i >= P are zero.
+ * without splitting it; ephdc_model_bytes = L n ceil(P/16) 32 R with R = 64 rows when
+ * k/k_in <= 8, else 128 (twice the residue model at k/k_in = 16 or 8).  Order: fp16
+ * tiles of R rows x 16 columns, tile ((l (n/8) + x/8) ceil(P/16) + i/16) 8 + x%8 for
+ * coefficient x of limb l and plaintext i; row (R/4) v + o, column i%16 at byte
+ * (row/8) 256 + (column/8) 128 + (row%8) 16 + (column%8) 2; rows of outputs
+ * o >= 2 k/k_in and columns of plaintexts i >= P are zero.
  * Set it before bfv_encrypt_model (or convert a residue model with
  * bfv_model_to_digits); the multiply-accumulate then runs "mac_mode" 4 (0 or 4 accepted,
  * others EPHDC_EUNSUPPORTED), and the seeded model message, the compact model, the

@@ -518,8 +518,8 @@ size_t ephdc_galois_key_bytes(const ephdc_ctx* c) {
 }
 size_t ephdc_model_bytes(const ephdc_ctx* c) {
   if (!c) return 0;
-  // the digit model: 4 KB per (limb, coefficient, 16 plaintexts)
-  if (c->dc.mdig) return (size_t)c->dc.L * c->dc.n * ((c->dc.P + 15) / 16) * 4096;
+  // the digit model: 2 KB (k/k_in <= 8) or 4 KB per (limb, coefficient, 16 plaintexts)
+  if (c->dc.mdig) return mdig_bytes(c->dc.n, c->dc.L, c->dc.P, c->dc.Kp);
   return (size_t)c->dc.P * c->dc.Kp * (c->dc.compact ? 1 : 2) * c->dc.L * c->dc.n *
          sizeof(uint32_t);
 }

@@ -46,8 +46,10 @@ constexpr int KB = 8;                       // coefficients per tile
 constexpr int GN = 16;                      // groups per tile (N = 4 digits x 16)
 constexpr int KC = 16;                      // plaintexts per step = MMA K
 constexpr int WINS = 64;                    // steps per exact window (1024 plaintexts)
-constexpr int A_TILE = 4096;                // model operand of one coefficient: 128 x 16 fp16
-constexpr int A_BYTES = KB * A_TILE;        // 32 KB per step
+// model operand of one coefficient: M x 16 fp16 (M = 128 rows: 4 digits x 32 outputs;
+// M = 64: 4 digits x 16 outputs, for k/k_in <= 8), and of a step's 8 coefficients
+template <int M> __host__ __device__ constexpr int a_tile() { return M * 32; }
+template <int M> __host__ __device__ constexpr int a_bytes() { return KB * a_tile<M>(); }
 constexpr int B_TILE = 2048;                // plaintext operand of one coefficient: 64 x 16
 constexpr int B_BYTES = KB * B_TILE;        // 16 KB per step
 constexpr int NA = 4;                       // model operand buffers (bulk-copy lookahead)
@@ -55,12 +57,18 @@ constexpr int NB = 2;                       // plaintext digit operand buffers
 constexpr int RAW_STEP = GN * KC * 32;      // 8 KB of 32-byte plaintext pieces per step
 constexpr int NS = 4;                       // cp.async ring stages
 constexpr int TCOLS = 512;
-// kind::f16 instruction descriptor: D = f32, A = B = f16, both K-major, N = 64, M = 128
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-constexpr size_t SMEM = 1024 + NA * A_BYTES + NB * B_BYTES + NS * RAW_STEP + 256;
+// kind::f16 instruction descriptor: D = f32, A = B = f16, both K-major, N = 64, M
+template <int M>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+template <int M>
+constexpr size_t smem_bytes() {
+  return 1024 + NA * (size_t)a_bytes<M>() + NB * B_BYTES + NS * RAW_STEP + 256;
+}
 constexpr long long WAIT_LIMIT = 1ll << 29;  // cycles (about a quarter of a second)
 static_assert(NB * B_BYTES >= 2 * 4 * 512 * 8, "the read-out staging lives in the B region");
-static_assert(SMEM <= 232448, "shared memory per CTA");
+static_assert(smem_bytes<128>() <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -104,11 +112,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) |
          ((uint64_t)(256 >> 4) << 32) | ((uint64_t)1 << 46);
 }
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc,
+                                       uint32_t id) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      "l"(a), "l"(b), "r"(id), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
@@ -216,13 +225,15 @@ __device__ __forceinline__ uint32_t sdigit_pair(uint32_t xb, uint32_t yb, uint32
 namespace {
 
 // 10 warps: an SM sub-partition holds 3 of them, so at most 168 registers per thread
+template <int M>
 __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t* __restrict__ pt,
                                                        const uint16_t* __restrict__ model,
                                                        uint32_t* __restrict__ out, int G,
                                                        uint32_t* status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* Areg = sm;                                        // [NA][8][128 x 16 fp16]
+  constexpr int A_TILE = a_tile<M>(), A_BYTES = a_bytes<M>();
+  uint8_t* Areg = sm;                                        // [NA][8][M x 16 fp16]
   uint8_t* Breg = Areg + NA * A_BYTES;                       // [NB][8][64 x 16 fp16]
   uint8_t* ring = Breg + NB * B_BYTES;                       // [NS][16 x 16 pieces of 32 B]
   uint64_t* fullA = (uint64_t*)(ring + NS * RAW_STEP);       // model operand landed
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
 #pragma unroll
         for (int j = 0; j < KB; j++)
           tc_mma(tmem + (uint32_t)(j * 64), sdesc(a0 + j * A_TILE), sdesc(b0 + j * B_TILE),
-                 first ? 0u : 1u);
+                 first ? 0u : 1u, idesc<M>());
         if (CL > 1) tc_commit_mc(smem_u32(&mfree[a]), cmask);
         else tc_commit(smem_u32(&mfree[a]));
         tc_commit(smem_u32(&doneB[b]));
@@ -415,8 +426,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
 #pragma unroll
     for (int j = 0; j < KB; j++) acc[j][0] = acc[j][1] = 0;
     int64_t* stage = reinterpret_cast<int64_t*>(Breg);  // [2 jj][4 v][16 g][32 o]
-    // read-out: warp w reads TMEM lanes 32 v + o (v = w % 4, output o = lane) of
-    // coefficients 2 p + w / 4, weighting the sum of digit pair (u, v) by 2^(8(u+v))
+    // read-out: warp w reads TMEM lanes 32 v + o (v = w % 4, output o = lane; with
+    // M = 64 only the first 16 lanes of each quarter, row 16 v + o, hold accumulators)
+    // of coefficients 2 p + w / 4, weighting the sum of digit pair (u, v) by 2^(8(u+v))
     const int qv = warp & 3, jj = warp >> 2;
     uint32_t tl = 0, tk0 = 0;  // the tile being accumulated
     int tg0 = 0;
@@ -452,7 +464,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
             t[g] += (int64_t)__float2int_rn(__uint_as_float(Sv[16 * u + g])) *
                     (int64_t)(int32_t)W[u];
 #pragma unroll
-        for (int g = 0; g < 16; g++) stage[(jj * 4 + qv) * 512 + g * 32 + lane] = t[g];
+        for (int g = 0; g < 16; g++)  // (M = 64: lanes 16-31 hold no accumulator)
+          stage[(jj * 4 + qv) * 512 + g * 32 + lane] = M == 128 || lane < 16 ? t[g] : 0;
         splitters_sync();
         // sum over v of the exact partial sums (|.| < 2^58), made non-negative with a
         // multiple of q_l above 2^58, and one reduction
@@ -531,13 +544,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
 
 namespace ephdc {
 
-cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint16_t* model,
-                          uint32_t* acc, int cluster, cudaStream_t st) {
-  if (2 * (int)c.Kp > 32 || c.n % KB || G < 1) return cudaErrorNotSupported;
+template <int M>
+static cudaError_t launch_uv(const DevCtx& c, const uint32_t* pt, int G, const uint16_t* model,
+                             uint32_t* acc, int cluster, cudaStream_t st) {
+  constexpr size_t SMEM = smem_bytes<M>();
   cudaError_t e =
-      cudaFuncSetAttribute(k_mac_uv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+      cudaFuncSetAttribute(k_mac_uv<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
   if (e != cudaSuccess) return e;
-  // a power of two (each CTA copies A_BYTES / cl bytes, a multiple of 16), at most the
+  // a power of two (each CTA copies a_bytes / cl bytes, a multiple of 16), at most the
   // power of two that covers the group blocks
   const int gb = (G + GN - 1) / GN;
   int cover = 1;
@@ -560,14 +574,14 @@ cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint
   cfg.numAttrs = 1;
   cfg.gridDim = dim3((unsigned)cl);
   // resident clusters per device and cluster size, asked once (a host-side query)
-  static int resident_cache[64][4];
+  static int resident_cache[64][4];  // per operand height (one instantiation each)
   int dev = 0;
   e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const int ci = cl == 1 ? 0 : cl == 2 ? 1 : cl == 4 ? 2 : 3;
   int resident = dev < 64 ? resident_cache[dev][ci] : 0;
   if (resident < 1) {
-    if (cudaOccupancyMaxActiveClusters(&resident, k_mac_uv, &cfg) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveClusters(&resident, k_mac_uv<M>, &cfg) != cudaSuccess ||
         resident < 1) {
       cudaGetLastError();
       int sms = 0;
@@ -578,7 +592,15 @@ cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint
   }
   const long long nc = tiles < resident ? tiles : resident;
   cfg.gridDim = dim3((unsigned)(nc * cl));
-  return cudaLaunchKernelEx(&cfg, k_mac_uv, c, pt, model, acc, G, c.status);
+  return cudaLaunchKernelEx(&cfg, k_mac_uv<M>, c, pt, model, acc, G, c.status);
+}
+
+cudaError_t launch_mac_uv(const DevCtx& c, const uint32_t* pt, int G, const uint16_t* model,
+                          uint32_t* acc, int cluster, cudaStream_t st) {
+  if (2 * (int)c.Kp > 32 || c.n % KB || G < 1) return cudaErrorNotSupported;
+  // the digit model's tile height (mdig_rows) is the MMA's M
+  return mdig_rows(c.Kp) == 64 ? launch_uv<64>(c, pt, G, model, acc, cluster, st)
+                               : launch_uv<128>(c, pt, G, model, acc, cluster, st);
 }
 
 }  // namespace ephdc

@@ -83,7 +83,7 @@ __device__ __forceinline__ void store_digits(const DevCtx& c, uint16_t* mdig, ui
   const uint32_t vb = val + 0x80808080u;
 #pragma unroll
   for (uint32_t v = 0; v < 4; v++)
-    mdig[mdig_index(c.n, c.P, i, o, v, l, x)] =
+    mdig[mdig_index(c.n, c.P, mdig_rows(c.Kp), i, o, v, l, x)] =
         __half_as_ushort(__int2half_rn((int)((vb >> (8 * v)) & 255u) - 128));
 }
 
@@ -400,7 +400,8 @@ __global__ void k_undigit(DevCtx c, const uint16_t* __restrict__ mdig, uint32_t*
     const uint32_t o = (uint32_t)(rest % O), i = (uint32_t)(rest / O);
     int64_t r = 0;
     for (uint32_t v = 0; v < 4; v++)
-      r += (int64_t)__half2int_rn(__ushort_as_half(mdig[mdig_index(c.n, c.P, i, o, v, l, k)]))
+      r += (int64_t)__half2int_rn(
+               __ushort_as_half(mdig[mdig_index(c.n, c.P, mdig_rows(c.Kp), i, o, v, l, k)]))
            << (8 * v);
     dst[x] = (uint32_t)r;
   }
@@ -441,7 +442,7 @@ cudaError_t launch_encrypt_model(const DevCtx& c, const int8_t* classes, const u
   cudaError_t e = set_smem(k_encrypt_model, s);
   if (e != cudaSuccess) return e;
   if (c.mdig) {  // the digit model's padding rows and plaintexts are zero
-    e = cudaMemsetAsync(model, 0, (size_t)c.L * c.n * ((c.P + 15) / 16) * 4096, st);
+    e = cudaMemsetAsync(model, 0, mdig_bytes(c.n, c.L, c.P, c.Kp), st);
     if (e != cudaSuccess) return e;
   }
   k_encrypt_model<<<dim3(c.P * c.Kp, c.L), ntt_threads(c), s, st>>>(c, classes, sk, seed, model);
@@ -499,7 +500,7 @@ cudaError_t launch_model_to_digits(const DevCtx& c, const uint32_t* model, uint1
                                    cudaStream_t st) {
   const size_t words = (size_t)c.P * 2 * c.Kp * c.L * c.n;
   cudaError_t e =
-      cudaMemsetAsync(mdig, 0, (size_t)c.L * c.n * ((c.P + 15) / 16) * 4096, st);
+      cudaMemsetAsync(mdig, 0, mdig_bytes(c.n, c.L, c.P, c.Kp), st);
   if (e != cudaSuccess) return e;
   k_todigits<<<1024, 256, 0, st>>>(c, model, mdig, words);
   return cudaGetLastError();

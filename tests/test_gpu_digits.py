@@ -35,8 +35,10 @@ def _digit_ctx(w, B, cluster=0, **kw):
     ctx.tune_set("model_digits", 1)
     assert ctx.tune_get("model_digits") == 1
     ctx.tune_set("mac_cluster", cluster)
-    # 4 KB of digit operand per (limb, coefficient, 16 plaintexts)
-    assert E.lib().ephdc_model_bytes(ctx.ctx) == w.L * w.n * ((ctx.P + 15) // 16) * 4096
+    # per (limb, coefficient, 16 plaintexts) an operand tile of 4 digits x 16 outputs
+    # (k/k_in <= 8) or x 32 outputs, 16 fp16 columns
+    rows = 64 if 2 * ctx.Kp <= 16 else 128
+    assert E.lib().ephdc_model_bytes(ctx.ctx) == w.L * w.n * ((ctx.P + 15) // 16) * rows * 32
     return ctx
 
 
