@@ -79,7 +79,7 @@ struct DevCtx {
   // digit model: the model is stored as the tensor-core operand of its signed base-256
   // digits, fp16 tiles [L][n/8][P16][8][R x 16] (P16 = ceil(P/16); R = mdig_rows(Kp):
   // 64 rows when k/k_in <= 8, else 128; tile (l, x/8, i/16, x%8) holds rows
-  // r = (R/4) v + o, columns i%16, at mdig_off(r, i%16); rows o >= O and plaintexts
+  // r = 4 o + v, columns i%16, at mdig_off(r, i%16); rows o >= O and plaintexts
   // i >= P are zero), read by the digit-outer-product multiply-accumulate
   uint32_t mdig;
 };
@@ -91,8 +91,8 @@ struct DevCtx {
 __host__ __device__ __forceinline__ uint32_t mdig_off(uint32_t r, uint32_t k) {
   return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
-// rows of a digit-model tile: 4 digits x 16 outputs (k/k_in <= 8, an M = 64 operand)
-// or 4 digits x 32 outputs (M = 128)
+// rows of a digit-model tile: 16 outputs x 4 digits (k/k_in <= 8, an M = 64 operand)
+// or 32 outputs x 4 digits (M = 128)
 __host__ __device__ __forceinline__ uint32_t mdig_rows(uint32_t Kp) {
   return 2 * Kp <= 16 ? 64u : 128u;
 }
@@ -102,13 +102,14 @@ __host__ __device__ __forceinline__ size_t mdig_bytes(uint32_t n, uint32_t L, ui
   return (size_t)L * n * ((P + 15) / 16) * mdig_rows(Kp) * 32;
 }
 // fp16 word index of digit v of model residue (plaintext i, output o, limb l,
-// coefficient x) in the digit model with R rows per tile
+// coefficient x) in the digit model with R rows per tile (row 4 o + v: the 4 digits of
+// an output sit in 4 consecutive accumulator lanes of one warp)
 __host__ __device__ __forceinline__ size_t mdig_index(uint32_t n, uint32_t P, uint32_t R,
                                                       uint32_t i, uint32_t o, uint32_t v,
                                                       uint32_t l, uint32_t x) {
   const uint32_t P16 = (P + 15) / 16;
   const size_t tile = (((size_t)l * (n >> 3) + (x >> 3)) * P16 + (i >> 4)) * 8 + (x & 7);
-  return tile * (R * 16) + mdig_off((R / 4) * v + o, i & 15) / 2;
+  return tile * (R * 16) + mdig_off(4 * o + v, i & 15) / 2;
 }
 
 // word index of coefficient k of limb l of pair (a, b) in the blocked layout

@@ -7,7 +7,7 @@
 // c = sum_v e_v 2^(8v) with d_u, e_v in [-128, 127] (the bytes of a + 0x80808080, each
 // less 128), so  a c = sum_{u,v} 2^(8(u+v)) d_u e_v.  One MMA per coefficient and 16
 // plaintexts computes every digit product at once: A holds the model digits, rows
-// (v, o) = 32 v + o (M = 128), B the plaintext digits, rows (u, g) = 16 u + g (N = 64),
+// (o, v) = 4 o + v (M = 128), B the plaintext digits, rows (u, g) = 16 u + g (N = 64),
 // and accumulator element ((v, o), (u, g)) collects sum_i e_v d_u.  Each product is at
 // most 2^14 in magnitude, so a window of 1024 plaintexts keeps every fp32 partial sum an
 // exact integer within 2^24.  After a window the sums are weighted by 2^(8(u+v)) mod q_l
@@ -46,8 +46,8 @@ constexpr int KB = 8;                       // coefficients per tile
 constexpr int GN = 16;                      // groups per tile (N = 4 digits x 16)
 constexpr int KC = 16;                      // plaintexts per step = MMA K
 constexpr int WINS = 64;                    // steps per exact window (1024 plaintexts)
-// model operand of one coefficient: M x 16 fp16 (M = 128 rows: 4 digits x 32 outputs;
-// M = 64: 4 digits x 16 outputs, for k/k_in <= 8), and of a step's 8 coefficients
+// model operand of one coefficient: M x 16 fp16 (M = 128 rows: 32 outputs x 4 digits;
+// M = 64: 16 outputs x 4 digits, for k/k_in <= 8), and of a step's 8 coefficients
 template <int M> __host__ __device__ constexpr int a_tile() { return M * 32; }
 template <int M> __host__ __device__ constexpr int a_bytes() { return KB * a_tile<M>(); }
 constexpr int B_TILE = 2048;                // plaintext operand of one coefficient: 64 x 16
@@ -67,7 +67,6 @@ constexpr size_t smem_bytes() {
   return 1024 + NA * (size_t)a_bytes<M>() + NB * B_BYTES + NS * RAW_STEP + 256;
 }
 constexpr long long WAIT_LIMIT = 1ll << 29;  // cycles (about a quarter of a second)
-static_assert(NB * B_BYTES >= 2 * 4 * 512 * 8, "the read-out staging lives in the B region");
 static_assert(smem_bytes<128>() <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -421,15 +420,24 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
                        sdigit_pair(x[4], x[5], u), sdigit_pair(x[6], x[7], u));
     };
 
-    // accumulators mod q_l: acc[j][m] for coefficient j and pair tid + 256 m = g * 32 + o
-    uint32_t acc[KB][2];
+    // read-out: warp w reads TMEM lanes 32 qv .. 32 qv + 31 (qv = w % 4) of coefficients
+    // 4 jj .. 4 jj + 3 (jj = w / 4).  Accumulator row 4 o + v sits in lane 4 o + v
+    // (M = 128) or, with M = 64, in lane 32 (r / 16) + r % 16 (lanes 16-31 of each
+    // quarter hold none), so lane (o, v) with v = lane % 4 and o = OQ qv + lane / 4 weights
+    // the sums of its digit pairs (u, v) by 2^(8(u+v)) mod q_l and the 4 lanes of an
+    // output add their partial sums by two exchanges, each lane keeping 4 of the 16
+    // groups: g = 8 b0 + 4 b1 + e for lane bits b0, b1 and e < 4.
+    constexpr int OQ = M / 16;  // outputs per 32-lane quarter
+    const int qv = warp & 3, jj = warp >> 2, dv = lane & 3;
+    const int b0 = lane & 1, b1 = (lane >> 1) & 1;
+    const int ro = OQ * qv + (lane >> 2), rg = 8 * b0 + 4 * b1;  // this lane's output, groups
+    const bool rown = M == 128 || lane < 16;                      // the lane holds accumulators
+    // accumulators mod q_l: acc[e2][e] for coefficient 4 jj + e2 and group rg + e
+    uint32_t acc[4][4];
 #pragma unroll
-    for (int j = 0; j < KB; j++) acc[j][0] = acc[j][1] = 0;
-    int64_t* stage = reinterpret_cast<int64_t*>(Breg);  // [2 jj][4 v][16 g][32 o]
-    // read-out: warp w reads TMEM lanes 32 v + o (v = w % 4, output o = lane; with
-    // M = 64 only the first 16 lanes of each quarter, row 16 v + o, hold accumulators)
-    // of coefficients 2 p + w / 4, weighting the sum of digit pair (u, v) by 2^(8(u+v))
-    const int qv = warp & 3, jj = warp >> 2;
+    for (int e2 = 0; e2 < 4; e2++)
+#pragma unroll
+      for (int e = 0; e < 4; e++) acc[e2][e] = 0;
     uint32_t tl = 0, tk0 = 0;  // the tile being accumulated
     int tg0 = 0;
     ModP m;
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
       tile_of(tau, tl, tk0, tg0);
       m = c.mq[tl < L ? tl : 0];
       uint32_t w = 1;
-      for (int s = 0; s < qv; s++) w = mulm(w, 256u, m);
+      for (int s = 0; s < dv; s++) w = mulm(w, 256u, m);
       for (int u = 0; u < 4; u++) {
         W[u] = w;
         w = mulm(w, 256u, m);
@@ -450,34 +458,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     };
     auto readout = [&]() {
 #pragma unroll
-      for (int p = 0; p < KB / 2; p++) {
-        const int j = 2 * p + jj;
-        int64_t t[16];
-#pragma unroll
-        for (int g = 0; g < 16; g++) t[g] = 0;
+      for (int e2 = 0; e2 < 4; e2++) {
         uint32_t Sv[64];  // column 16 u + g: digit pair (u, v), group g
-        tc_ld64(tmem + ((uint32_t)(32 * qv) << 16) + (uint32_t)(j * 64), Sv);
+        tc_ld64(tmem + ((uint32_t)(32 * qv) << 16) + (uint32_t)((4 * jj + e2) * 64), Sv);
+        // exact partial sums in two's complement (lanes without accumulators wrap
+        // harmlessly and are never stored)
+        uint64_t t[16];
 #pragma unroll
-        for (int u = 0; u < 4; u++)
+        for (int g = 0; g < 16; g++) {
+          t[g] = 0;
 #pragma unroll
-          for (int g = 0; g < 16; g++)
-            t[g] += (int64_t)__float2int_rn(__uint_as_float(Sv[16 * u + g])) *
-                    (int64_t)(int32_t)W[u];
+          for (int u = 0; u < 4; u++)
+            t[g] += (uint64_t)((int64_t)__float2int_rn(__uint_as_float(Sv[16 * u + g])) *
+                               (int64_t)(int32_t)W[u]);
+        }
+        // sum over the 4 digits v of the output: keep half of the groups, add the
+        // partner's half, twice
+        uint64_t h[8];
 #pragma unroll
-        for (int g = 0; g < 16; g++)  // (M = 64: lanes 16-31 hold no accumulator)
-          stage[(jj * 4 + qv) * 512 + g * 32 + lane] = M == 128 || lane < 16 ? t[g] : 0;
-        splitters_sync();
-        // sum over v of the exact partial sums (|.| < 2^58), made non-negative with a
-        // multiple of q_l above 2^58, and one reduction
+        for (int g = 0; g < 8; g++) {
+          const uint64_t keep = b0 ? t[g + 8] : t[g], send = b0 ? t[g] : t[g + 8];
+          h[g] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+        }
 #pragma unroll
-        for (int mm = 0; mm < 2; mm++)
-#pragma unroll
-          for (int j2 = 0; j2 < 2; j2++) {
-            const int64_t* st = stage + j2 * 4 * 512 + tid + SPLITTERS * mm;
-            const uint64_t v = (uint64_t)(st[0] + st[512] + st[1024] + st[1536]) + OFF;
-            acc[2 * p + j2][mm] = addm(acc[2 * p + j2][mm], red64(v, m.p, m.mu), m.p);
-          }
-        splitters_sync();
+        for (int e = 0; e < 4; e++) {
+          const uint64_t keep = b1 ? h[e + 4] : h[e], send = b1 ? h[e] : h[e + 4];
+          const uint64_t v = keep + __shfl_xor_sync(0xffffffffu, send, 2) + OFF;
+          acc[e2][e] = addm(acc[e2][e], red64(v, m.p, m.mu), m.p);
+        }
       }
     };
 
@@ -506,19 +514,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
         mbar_arrive(smem_u32(tfree));
       }
       if (++s == S) {
-        // the tile's 8 consecutive coefficients of (group, output): two 16-byte stores
+        // coefficients 4 jj .. 4 jj + 3 of (group rg + e, output ro): one 16-byte store each
 #pragma unroll
-        for (int mm = 0; mm < 2; mm++) {
-          const int pair = tid + SPLITTERS * mm, g = pair >> 5, o = pair & 31;
-          if (alive && tg0 + g < G && o < O) {
+        for (int e = 0; e < 4; e++) {
+          if (alive && rown && tg0 + rg + e < G && ro < O) {
             uint4* dst = reinterpret_cast<uint4*>(
-                out + (((size_t)(tg0 + g) * O + o) * L + tl) * n + tk0);
-            dst[0] = make_uint4(acc[0][mm], acc[1][mm], acc[2][mm], acc[3][mm]);
-            dst[1] = make_uint4(acc[4][mm], acc[5][mm], acc[6][mm], acc[7][mm]);
+                out + (((size_t)(tg0 + rg + e) * O + ro) * L + tl) * n + tk0 + 4 * jj);
+            *dst = make_uint4(acc[0][e], acc[1][e], acc[2][e], acc[3][e]);
           }
         }
 #pragma unroll
-        for (int j = 0; j < KB; j++) acc[j][0] = acc[j][1] = 0;
+        for (int e2 = 0; e2 < 4; e2++)
+#pragma unroll
+          for (int e = 0; e < 4; e++) acc[e2][e] = 0;
         s = 0;
         if (++tau < T) start_tile(tau);
       }
