@@ -321,7 +321,7 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * without splitting it; ephdc_model_bytes = L n ceil(P/16) 32 R with R = 64 rows when
  * k/k_in <= 8, else 128 (twice the residue model at k/k_in = 16 or 8).  Order: fp16
  * tiles of R rows x 16 columns, tile ((l (n/8) + x/8) ceil(P/16) + i/16) 8 + x%8 for
- * coefficient x of limb l and plaintext i; row (R/4) v + o, column i%16 at byte
+ * coefficient x of limb l and plaintext i; row 4 o + v, column i%16 at byte
  * (row/8) 256 + (column/8) 128 + (row%8) 16 + (column%8) 2; rows of outputs
  * o >= 2 k/k_in and columns of plaintexts i >= P are zero.
  * Set it before bfv_encrypt_model (or convert a residue model with
