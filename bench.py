@@ -298,6 +298,9 @@ def run_ours(args, w, B):
                for i, b in enumerate(w.clients)] for s in range(R)]
         Xd = [[x.to(dev) for x in xs] for xs in Xh]
         pipe = BT.GraphedPipeline(ctx, Wt, model, gk, max_groups=ctx.groups(B))
+        hdc = {}
+        if args.hdc_mode < 0:  # the HDC projection kernel, timed on this batch
+            hdc, _, _ = AT.tune_hdc(ctx, torch.cat(Xd[0]), Wt, reps=3)
         pt0 = ctx.encode_plain(ctx.hdc_encode(torch.cat(Xd[0]), Wt))
         if args.mac_mode >= 0:
             tuned = {"mac_mode": args.mac_mode}
@@ -306,7 +309,7 @@ def run_ours(args, w, B):
         del pt0
         out = pipe.out
         enc, _, _ = AT.tune_encode(ctx, ctx.hdc_encode(torch.cat(Xd[0]), Wt), reps=3)
-        tuned = {**tuned, **enc}
+        tuned = {**tuned, **enc, **hdc}
         # consecutive steps alternate over S pipelines (each its own context, graphs and
         # stream, sharing the model and keys), so one step's MAC and rotations overlap
         # the next step's encoding
@@ -332,8 +335,12 @@ def run_ours(args, w, B):
         Xd = [x.to(dev) for x in Xh]
         out = ctx.out_ct(B)
         from paper_2511_00737_gb300 import autotune as AT
+        hdc = {}
+        if args.hdc_mode < 0:  # the HDC projection kernel, timed on this batch
+            hdc, _, _ = AT.tune_hdc(ctx, Xd[0], Wt, reps=5)
         H0 = ctx.hdc_encode(Xd[0], Wt)
         tuned, _, _ = AT.tune_encode(ctx, H0, reps=5)  # pass schedule of the transforms
+        tuned = {**tuned, **hdc}
         if args.mac_tile >= 0:
             tuned = {**tuned, "mac_mode": 2, "mac_tile": args.mac_tile}
             AT.apply(ctx, tuned)

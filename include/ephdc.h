@@ -287,10 +287,11 @@ ephdc_status ephdc_find_dmax_trial(ephdc_ctx* ctx, const void* sk_dev, const int
  * consecutive group blocks that share each model block by multicast, 0 = 4), "mac_min_groups" and "mac_tc_min_groups" (tiled, tensor
  * cores from this many groups on in automatic mode), "mac_splits" (streaming split cap, 0 =
  * heuristic), "mac_tile" = gt*10^6 + ot*10^4 + gc*100 + ic (groups and outputs per
- * warp, groups per CTA, plaintexts per staged chunk, at most 15); "hdc_mode" 0..3 is
+ * warp, groups per CTA, plaintexts per staged chunk, at most 15); "hdc_mode" 0..4 is
  * the HDC projection kernel (persistent tensor-core GEMM with 128 x 256 tiles and a
  * 3-stage ring / one 128 x 128 tile per CTA / persistent with 128 x 128 tiles /
- * persistent 128 x 256 with a 4-stage ring);
+ * persistent 128 x 256 with a 4-stage ring / mode 0 in clusters of two CTAs that take
+ * row blocks 2m and 2m + 1 of the same 256 columns and share each W slice by multicast);
  * "ntt_plan" 0/1/2
  * is the pass schedule of the encoding transforms (balanced, radix-32 passes first,
  * radix-32 passes last).  "layout" 0/1 is the device order of the NTT-domain

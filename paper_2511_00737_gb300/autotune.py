@@ -8,6 +8,8 @@ over plaintext ranges (several split caps), and the tiled multi-group kernel wit
 2 or 4 groups and 4, 7 or 8 outputs per warp, 8 to 64 groups per CTA and 4 to 15
 plaintexts per staged chunk, and the exact signed-digit product on the tensor cores
 (the only candidate when the context stores plaintexts and model coefficient-blocked).
+It also picks the encoder's pass schedule (tune_encode) and the HDC projection kernel
+(tune_hdc) by timing each.
 A context with the digit model has one product, the digit outer product on the tensor
 cores; its candidates are the cluster sizes that share each model block.
 """
@@ -136,6 +138,37 @@ def tune_encode(ctx, H, reps=5, use_cache=True):
         ctx.tune_set("ntt_plan", v)
         ms = _time(lambda: ctx.encode_plain(H), reps)
         table.append((ms, {"ntt_plan": v}))
+    table.sort(key=lambda x: x[0])
+    best_ms, best = table[0]
+    apply(ctx, best)
+    if use_cache:
+        cache = _load()
+        cache[key] = {"knobs": best, "ms": best_ms}
+        _save(cache)
+    return best, best_ms, table
+
+
+def tune_hdc(ctx, X, Wt, reps=5, use_cache=True):
+    """Pick the fastest HDC projection kernel (knob hdc_mode: persistent 128 x 256 tiles
+    with 3 or 4 stages, in clusters of two sharing each W slice, 128 x 128 tiles, one
+    tile per CTA) for this batch; a kernel the device refuses to launch is skipped."""
+    B = X.shape[0]
+    key = _key(ctx, ctx.groups(B)) + "|hdc|F%d|D%d" % (ctx.F, ctx.D)
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        apply(ctx, cache[key]["knobs"])
+        return cache[key]["knobs"], cache[key]["ms"], []
+    from .ephdc import EphdcError
+    table = []
+    for v in (0, 1, 2, 3, 4):
+        try:
+            ctx.tune_set("hdc_mode", v)
+            ms = _time(lambda: ctx.hdc_encode(X, Wt), reps)
+        except EphdcError:
+            continue
+        table.append((ms, {"hdc_mode": v}))
+    if not table:
+        raise RuntimeError("no HDC projection kernel could be launched")
     table.sort(key=lambda x: x[0])
     best_ms, best = table[0]
     apply(ctx, best)

@@ -1099,7 +1099,7 @@ ephdc_status ephdc_tune_set(ephdc_ctx* c, const char* knob, int64_t v) {
     if (v < 0 || v > 2) return fail(c, EPHDC_EINVAL, "ntt_plan must be 0, 1 or 2");
     c->dc.ntt_plan = (int32_t)v;
   } else if (!strcmp(knob, "hdc_mode")) {
-    if (v < 0 || v > 3) return fail(c, EPHDC_EINVAL, "hdc_mode must be 0, 1, 2 or 3");
+    if (v < 0 || v > 4) return fail(c, EPHDC_EINVAL, "hdc_mode must be 0 .. 4");
     c->dc.hdc_mode = (int32_t)v;
   } else if (!strcmp(knob, "mac_tc_min_groups")) {
     if (v < 1) return fail(c, EPHDC_EINVAL, "mac_tc_min_groups must be >= 1");

@@ -80,6 +80,25 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
       : "memory");
 }
+// the same box into this CTA and every CTA of `mask` (same shared-memory offset), each
+// copy completing on the mbarrier at `bar`'s offset in its CTA
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
@@ -103,6 +122,15 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+      : "memory");
+}
+// arrive on the mbarrier at `bar`'s offset in every CTA of `mask` once the MMAs issued
+// so far are complete
+__device__ __forceinline__ void tc_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;\n" ::"r"(bar),
+      "h"(mask)
       : "memory");
 }
 // load and wait in one statement, so that no use of the registers can be scheduled
@@ -247,11 +275,16 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
 }
 
-template <int PN, int PS>
+// CL = 2: the two CTAs of a cluster take the tiles (2 m, n) and (2 m + 1, n) of tile
+// pair (m, n); each loads its own X slice and half of the shared W slice (tb: a box of
+// PN / 2 rows), multicast to both, and each MMA lane frees a stage in both CTAs, so a
+// stage is refilled only after both have consumed it (empty barriers count 2).
+template <int PN, int PS, int CL = 1>
 __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtensorMap ta,
                                                  const __grid_constant__ CUtensorMap tb, int B,
                                                  int D, int F, int shift, int bits,
                                                  int8_t* __restrict__ H, uint32_t* status) {
+  static_assert(CL == 1 || CL == 2, "clusters of 1 or 2 CTAs");
   using Sh = PersistentShape<PN, PS>;
   constexpr int STAGES = PS, TN = PN;
   constexpr uint32_t B_BYTES = Sh::B_BYTES, STAGE_BYTES = Sh::STAGE;
@@ -266,7 +299,16 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (F + TK - 1) / TK;
   const int ntn = (D + TN - 1) / TN, ntm = (B + TM - 1) / TM;
-  const int ntiles = ntn * ntm;
+  // work items: tiles (CL = 1) or tile pairs sharing a W slice (CL = 2), walked by
+  // CTA (cluster) `first` with stride `stride`
+  const uint32_t rank = CL > 1 ? cluster_ctarank() : 0u;
+  const int ntiles = ntn * ((ntm + CL - 1) / CL);
+  const int first = (int)blockIdx.x / CL, stride = (int)gridDim.x / CL;
+  auto tile_mn = [&](int t, int& m0, int& n0) {
+    m0 = ((t / ntn) * CL + (int)rank) * TM;
+    n0 = (t % ntn) * TN;
+  };
+  constexpr uint16_t CMASK = (uint16_t)((1u << CL) - 1u);
   auto full = [&](int s) { return smem_u32(&bars[s]); };
   auto empty = [&](int s) { return smem_u32(&bars[STAGES + s]); };
   auto tfull = [&](int a) { return smem_u32(&bars[2 * STAGES + a]); };
@@ -276,7 +318,7 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; s++) {
       mbar_init(full(s), 1);
-      mbar_init(empty(s), 1);
+      mbar_init(empty(s), CL);
     }
     for (int a = 0; a < 2; a++) {
       mbar_init(tfull(a), 1);
@@ -294,6 +336,7 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_sync_all();  // both CTAs' barriers exist before either signals
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -301,17 +344,22 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
     // producer
     int it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-      const int m0 = (tile / ntn) * TM, n0 = (tile % ntn) * TN;
+    for (int tile = first; ok && tile < ntiles; tile += stride) {
+      int m0, n0;
+      tile_mn(tile, m0, n0);
       for (int k = 0; k < nk; k++, it++) {
         const int s = it % STAGES;
         if (it >= STAGES && !mbar_wait(empty(s), ((it / STAGES) - 1) & 1, status, 4)) {
           ok = false;
           break;
         }
-        mbar_expect_tx(full(s), STAGE_BYTES);
+        mbar_expect_tx(full(s), STAGE_BYTES);  // (CL = 2: both halves of the W slice)
         tma_load_2d(smem_u32(sA + s * A_BYTES), &ta, k * TK, m0, full(s));
-        tma_load_2d(smem_u32(sB + s * B_BYTES), &tb, k * TK, n0, full(s));
+        if (CL == 1)
+          tma_load_2d(smem_u32(sB + s * B_BYTES), &tb, k * TK, n0, full(s));
+        else
+          tma_load_2d_mc(smem_u32(sB + s * B_BYTES + rank * (B_BYTES / CL)), &tb, k * TK,
+                         n0 + (int)rank * (TN / CL), full(s), CMASK);
       }
     }
     // the copies still in flight land before the CTA can exit (complete already unless
@@ -322,7 +370,7 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
     // MMA issuer
     int it = 0, j = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, j++) {
+    for (int tile = first; ok && tile < ntiles; tile += stride, j++) {
       const int a = j & 1;
       if (j >= 2 && !mbar_wait(tempty(a), ((j >> 1) - 1) & 1, status, 5)) break;
       tc_fence_after();
@@ -339,7 +387,8 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
         for (int kk = 0; kk < TK / 16; kk++)
           tc_mma(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), (k | kk) != 0,
                  IDESC_P);
-        tc_commit(empty(s));
+        if (CL == 1) tc_commit(empty(s));
+        else tc_commit_mc(empty(s), CMASK);
       }
       if (ok) tc_commit(tfull(a));
     }
@@ -351,12 +400,13 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
     const int rnd = shift > 0 ? 1 << (shift - 1) : 0;
     const int lo = -(1 << (bits - 1)), hi = (1 << (bits - 1)) - 1;
     int j = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, j++) {
+    for (int tile = first; tile < ntiles; tile += stride, j++) {
       const int a = j & 1;
       const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull(a), (j >> 1) & 1, status, 5));
       if (!ready) break;
       tc_fence_after();
-      const int m0 = (tile / ntn) * TM, n0 = (tile % ntn) * TN;
+      int m0, n0;
+      tile_mn(tile, m0, n0);
       const int row = m0 + 32 * (int)q + (int)lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < TN; c0 += 32) {
@@ -394,6 +444,16 @@ __global__ void __launch_bounds__(192) k_hdc_tcp(const __grid_constant__ CUtenso
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
                  "r"(Sh::TMEM_COLS)
                  : "memory");
+  if (CL > 1) {
+    // after a recorded failure some waits were skipped: give the peer's copies and
+    // commits already issued 50 us to land, then leave together
+    if (threadIdx.x == 0 && *(volatile uint32_t*)status != 0u) {
+      const long long t0 = clock64();
+      while (clock64() - t0 < 100000ll) __nanosleep(1000);
+    }
+    __syncwarp();  // the aligned cluster barrier wants the whole warp converged
+    cluster_sync_all();
+  }
 }
 
 // int8 -> fp16, 16 elements per thread (n16 chunks of 16)
@@ -503,8 +563,8 @@ cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt
   if (c.hdc_mode != 1) {
     // persistent: 128 x 256 tiles with all 512 TMEM columns, one CTA per SM, and a
     // 3-stage ring of 145 KB that leaves room on the SM for an encoder CTA of another
-    // stream (mode 0) or a 4-stage ring of 193 KB (mode 3); or 128 x 128 tiles, two
-    // CTAs per SM (mode 2)
+    // stream (mode 0), the same in clusters of two sharing each W slice (mode 4) or a
+    // 4-stage ring of 193 KB (mode 3); or 128 x 128 tiles, two CTAs per SM (mode 2)
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -524,6 +584,42 @@ cudaError_t launch_hdc_encode(const DevCtx& c, const int8_t* X, const int8_t* Wt
                                           c.status);
       return cudaGetLastError();
     };
+    if (c.hdc_mode == 4) {
+      // clusters of two CTAs sharing each W slice: W boxes of 128 rows, one per rank,
+      // multicast to both; as many clusters as are resident at once
+      e = tensor_map(&tb, c.wh, c.F, c.D, 128);
+      if (e != cudaSuccess) return e;
+      constexpr uint32_t SM4 = PersistentShape<256, 3>::SMEM;
+      auto kern = k_hdc_tcp<256, 3, 2>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SM4);
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 2;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.blockDim = dim3(192);
+      cfg.dynamicSmemBytes = SM4;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cfg.gridDim = dim3(2);
+      static int resident_cache[64];  // resident clusters per device, asked once
+      int resident = dev < 64 ? resident_cache[dev] : 0;
+      if (resident < 1) {
+        if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) != cudaSuccess ||
+            resident < 1) {
+          cudaGetLastError();
+          resident = sms / 2 > 0 ? sms / 2 : 1;
+        }
+        if (dev < 64) resident_cache[dev] = resident;
+      }
+      const int pairs = (int)((c.D + 255) / 256) * ((B + 2 * TM - 1) / (2 * TM));
+      cfg.gridDim = dim3((unsigned)(2 * (pairs < resident ? pairs : resident)));
+      return cudaLaunchKernelEx(&cfg, kern, ta, tb, B, (int)c.D, (int)c.F, c.shift, (int)c.bits,
+                                H, c.status);
+    }
     if (c.hdc_mode == 0) return launch(k_hdc_tcp<256, 3>, PersistentShape<256, 3>::SMEM);
     if (c.hdc_mode == 3) return launch(k_hdc_tcp<256, 4>, PersistentShape<256, 4>::SMEM);
     return launch(k_hdc_tcp<128, 3>, PersistentShape<128, 3>::SMEM);

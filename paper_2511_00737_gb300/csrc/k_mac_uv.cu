@@ -545,6 +545,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mac_uv(DevCtx c, const uint32_t*
     const long long t0 = clock64();
     while (clock64() - t0 < 100000ll) __nanosleep(1000);
   }
+  __syncwarp();    // the aligned cluster barrier wants the whole warp converged
   cluster_sync();  // no CTA leaves while a peer may still signal or fill it
 }
 

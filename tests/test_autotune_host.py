@@ -94,3 +94,49 @@ def test_tuner_skips_schedules_the_device_refuses(monkeypatch):
     ctx = TunableCtx(refuse={1, 2, 4})
     with pytest.raises(RuntimeError, match="no multiply-accumulate schedule"):
         AT.tune_similarity(ctx, None, 64, None, None, use_cache=False)
+
+
+def test_hdc_tuner_picks_the_fastest_kernel_and_skips_refused_ones(monkeypatch):
+    """tune_hdc times every HDC projection kernel (hdc_mode 0..4), skips one the device
+    refuses (e.g. a cluster it cannot place), applies the fastest and keys its cache by
+    the projection's shape as well."""
+    from paper_2511_00737_gb300.ephdc import EphdcError
+
+    class HdcCtx(FakeCtx):
+        def __init__(self, refuse):
+            super().__init__()
+            self.D, self.F, self.refuse = 10000, 608, refuse
+            self.knobs["hdc_mode"] = 0
+
+        def groups(self, B):
+            return B // 1024
+
+        def tune_set(self, k, v):
+            self.knobs[k] = v
+
+        def hdc_encode(self, X, Wt):
+            if self.knobs["hdc_mode"] in self.refuse:
+                raise EphdcError(-4, "cluster cannot be placed")
+
+    times = {0: 0.20, 1: 0.26, 2: 0.23, 3: 0.21, 4: 0.19}
+
+    def timed(fn, reps):
+        fn()
+        return times[ctx.knobs["hdc_mode"]]
+
+    class X:
+        shape = (16384, 608)
+
+    monkeypatch.setattr(AT, "_time", timed)
+    monkeypatch.setattr(AT.torch.cuda, "get_device_name", lambda d: "GPU X")
+    ctx = HdcCtx(refuse=set())
+    best, ms, table = AT.tune_hdc(ctx, X, None, use_cache=False)
+    assert best == {"hdc_mode": 4} and ms == 0.19 and len(table) == 5
+    assert ctx.knobs["hdc_mode"] == 4
+    ctx = HdcCtx(refuse={4})
+    best, ms, table = AT.tune_hdc(ctx, X, None, use_cache=False)
+    assert best == {"hdc_mode": 0} and [k["hdc_mode"] for _, k in table] == [0, 3, 2, 1]
+    assert ctx.knobs["hdc_mode"] == 0
+    ctx = HdcCtx(refuse={0, 1, 2, 3, 4})
+    with pytest.raises(RuntimeError, match="no HDC projection kernel"):
+        AT.tune_hdc(ctx, X, None, use_cache=False)

@@ -56,6 +56,8 @@ LAYOUTS = [
     (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 1),     # the same without clusters
     (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 2),     # clusters of 2
     (1024, 2, 4, 1, 8, 160, 32, 8, 8957, 8),     # one cluster of 8 (3 CTAs without groups)
+    (1024, 2, 8, 1, 4, 200, 32, 8, 4000, 0),     # 16 outputs: every lane 0-15 of a 64-row tile
+    (1024, 2, 9, 1, 4, 200, 32, 8, 4000, 0),     # 18 outputs: the smallest 128-row tile
 ]
 
 

@@ -113,13 +113,17 @@ def test_hdc_encode_matches_oracle(small):
     assert np.array_equal(small.g_H.cpu().numpy(), small.H)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3])  # persistent 128x256 (3 / 4 stages: 0 / 3), one tile per CTA, persistent 128x128
+# persistent 128x256 (3 / 4 stages: 0 / 3; clusters of two sharing each W slice: 4), one
+# tile per CTA (1), persistent 128x128 (2)
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("B,D,F,bits,shift", [(1, 257, 16, 8, 0), (300, 1000, 96, 4, 6),
                                               (129, 130, 608, 8, 5), (2000, 64, 1024, 2, 9),
                                               (8000, 1200, 608, 8, 5)])
 def test_hdc_encode_ragged_shapes(B, D, F, bits, shift, mode):
     """Ragged rows and columns; the last shape has 630 output tiles, so each persistent
-    CTA (two per SM) takes two or three tiles and reuses its TMEM accumulators."""
+    CTA (two per SM) takes two or three tiles and reuses its TMEM accumulators.  In
+    clusters of two (mode 4) an odd count of 128-row blocks leaves the second CTA of
+    the last pairs without rows, and D = 64 leaves its half of every W slice empty."""
     ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
     ctx.tune_set("hdc_mode", mode)
     X = WL.features(B + D, B, F)
@@ -140,7 +144,7 @@ def test_hdc_encode_extreme_magnitudes_exact():
     X[:64] = 127
     Wt[:100] = -1
     Wt[100:200] = 1
-    for shift, bits, mode in [(0, 8, 0), (10, 8, 1), (14, 4, 2)]:
+    for shift, bits, mode in [(0, 8, 0), (10, 8, 1), (14, 4, 2), (5, 8, 4)]:
         ctx = E.Context(1024, 2, 2, 1, 1, D, F, bits, shift, B)
         ctx.tune_set("hdc_mode", mode)
         H = ctx.hdc_encode(_dev(X), _dev(Wt))
