@@ -227,13 +227,6 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, boo
                "r"(ok ? 16 : 0));
 }
 
-// (hi:lo) += a * b as one carry chain: mad.lo.cc then madc.hi
-__device__ __forceinline__ void mac64(uint32_t& lo, uint32_t& hi, uint32_t a, uint32_t b) {
-  asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;\n"
-      : "+r"(lo), "+r"(hi)
-      : "r"(a), "r"(b));
-}
-
 // A chunked pass (several calls over plaintext ranges) reads plaintexts
 // [mi0, mi0 + cnt) of the model against a plaintext buffer of pP plaintexts per group
 // and adds into the accumulators (accum != 0) instead of overwriting them.
@@ -312,14 +305,15 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
     asm volatile("cp.async.commit_group;\n");
   };
 
-  // 64-bit accumulators as (lo, hi) words; each product (< 2^60) is added with a
-  // two-instruction carry chain, and the sums are reduced once per staged chunk
-  // (IC <= 15 products on top of a reduced value stay below 2^64)
-  uint32_t alo[GT][OT], ahi[GT][OT];
+  // 64-bit accumulators: each product (< 2^60) is added as one 64-bit multiply-add
+  // (no carry flag shared between accumulators, so their chains interleave), and the
+  // sums are reduced once per staged chunk (IC <= 15 products on top of a reduced value
+  // stay below 2^64)
+  uint64_t a64[GT][OT];
 #pragma unroll
   for (int x = 0; x < GT; x++)
 #pragma unroll
-    for (int y = 0; y < OT; y++) alo[x][y] = ahi[x][y] = 0;
+    for (int y = 0; y < OT; y++) a64[x][y] = 0;
   const int gb = wg * GT, ob = wo * OT;
   const int nchunks = (int)((CNT + IC - 1) / IC);
   load_chunk(0, 0);
@@ -344,15 +338,12 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
 #pragma unroll
       for (int g = 0; g < GT; g++)
 #pragma unroll
-        for (int o = 0; o < OT; o++) mac64(alo[g][o], ahi[g][o], x[g], y[o]);
+        for (int o = 0; o < OT; o++) a64[g][o] += (uint64_t)x[g] * y[o];
     }
 #pragma unroll
     for (int g = 0; g < GT; g++)
 #pragma unroll
-      for (int o = 0; o < OT; o++) {
-        alo[g][o] = red64(((uint64_t)ahi[g][o] << 32) | alo[g][o], p, mu);
-        ahi[g][o] = 0;
-      }
+      for (int o = 0; o < OT; o++) a64[g][o] = red64(a64[g][o], p, mu);
     __syncthreads();  // the buffer is refilled two chunks later
   }
 #pragma unroll
@@ -363,7 +354,7 @@ __global__ void __launch_bounds__(512) k_mac_tiled(DevCtx c, const uint32_t* __r
     for (int o = 0; o < OT; o++) {
       if (ob + o >= O) continue;
       uint32_t* a = acc + (((size_t)gg * O + ob + o) * L + l) * n + k0 + lane;
-      *a = accum ? csub(*a + alo[g][o], p) : alo[g][o];
+      *a = accum ? csub(*a + (uint32_t)a64[g][o], p) : (uint32_t)a64[g][o];
     }
   }
 }
