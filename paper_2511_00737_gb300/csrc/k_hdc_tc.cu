@@ -251,8 +251,9 @@ __global__ void __launch_bounds__(128) k_hdc_tc(const __grid_constant__ CUtensor
 
 // Persistent form: a grid of (at most) one CTA per SM with 128 x 256 output tiles (two
 // 256-column accumulators fill the SM's TMEM; a ring of 48 KB stages), or two CTAs per
-// SM with 128 x 128 tiles, walks the output tiles round-robin.  Six warps with fixed
-// roles:
+// SM with 128 x 128 tiles, walks the output tiles round-robin; or clusters of two such
+// CTAs walk pairs of tiles that share their 256 columns, each CTA staging one half of
+// the W slice into both (multicast).  Six warps with fixed roles:
 //   warp 0 (one lane): TMA producer, streaming the K slices of successive tiles through
 //                      the 3-stage ring without a break at tile boundaries;
 //   warp 1 (one lane): MMA issuer, accumulating tile j in TMEM buffer j % 2;
